@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the CHFPE hot path on B300: one step = one 2D response R2(t2, t1) (Eq. 2Dresponse)
+of the two-mode workload (2 coupled anharmonic modes, 32^4 grid, depth 4 = 15 members, LL + SL
+coupling, dt = 0.005, 64 x 64 samples at dtau = 0.2, all 64 t1 branches advanced in one batched
+launch per RK4 stage), FP32 state and arithmetic, FP64 reductions.
+
+Prints one JSON line (rank 0).  Metric: CHFPE cell-updates/s (one cell-update = one RK4 step of
+one (grid point, hierarchy member)), plus 2D spectra/s.  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+
+Timing: W warm-up steps, then K steps bracketed by a barrier and torch.cuda.synchronize(), CUDA
+events on the library's stream; inputs (3 x 64 branch states, 12 GB) are far larger than L2.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2509_25840_b300 import inputs  # noqa: E402
+
+ELEM_ACCESSES_PER_CELL_STEP = 11      # Horner-form RK4: 2 + 3 + 3 + 3 element accesses
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nt", type=int, default=64, help="t1/t2 samples (64 is the workload)")
+    ap.add_argument("--eq-steps", type=int, default=200, help="FP64 equilibration steps")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------
+# distributed plumbing (independent replicas: one spectrum per rank, no data-path collective)
+# ------------------------------------------------------------------------------------------
+
+def dist_setup(n: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("CHFPE_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, value: float, device=None) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# ------------------------------------------------------------------------------------------
+
+def oracle_sample(wl, nsteps: int = 1):
+    """Time `nsteps` FP64 RK4 steps of one full-size state with the oracle; cell-updates/s."""
+    import numpy as np
+    import oracle
+    pb = oracle.Problem(wl.model, wl.grid, wl.depth)
+    W = oracle.boltzmann(pb)
+    W = oracle.insert(pb, wl.A, W)
+    t0 = time.perf_counter()
+    oracle.rk4(pb, W, wl.dt, nsteps)
+    dt = time.perf_counter() - t0
+    cells = pb.M * pb.P
+    return cells * nsteps / dt, dt, oracle.threads(), np.isfinite(W).all()
+
+
+def run_reference(args, rank, world):
+    wl = inputs.two_mode_32(nt=args.nt)
+    if rank != 0:
+        return
+    times = []
+    for i in range(args.warmup + args.steps):
+        rate, dt, threads, _ = oracle_sample(wl, 1)
+        if i >= args.warmup:
+            times.append(dt)
+    T = sum(times)
+    cells = wl.cells * args.steps
+    value = cells / T
+    sample = (f"1 FP64 RK4 step of one 32^4 x 15-member state per bench step "
+              f"({wl.cells} cell-updates), oracle = plain C loops")
+    line = {
+        "impl": "reference", "metric": "CHFPE cell-updates/s", "value": value,
+        "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "cells": wl.cells, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local, pg):
+    import numpy as np
+    import torch
+    from paper_2509_25840_b300 import chfpe
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    wl = inputs.two_mode_32(nt=args.nt)
+    nt1 = nt2 = args.nt
+    h = chfpe.Handle(wl.model, wl.grid, depth=wl.depth, dt=wl.dt, precision=32,
+                     max_batch=nt1, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    eq_steps, eq_res = h.equilibrate(args.eq_steps, 1e-10, max(1, args.eq_steps))
+    eq_s = time.perf_counter() - t0
+    R = np.empty((nt1, nt2))
+    spectrum_cells = wl.cells * ((nt1 - 1) * wl.stride + nt1 * (nt2 - 1) * wl.stride)
+
+    def step():
+        h.response2(wl.A, wl.B, wl.C, nt1, nt2, wl.stride, out=R)
+
+    for _ in range(args.warmup):
+        step()
+    R_warm = R.copy()
+
+    # device-resident inputs: the equilibrium stays in HBM, R (32 KB) comes back each step
+    clocks = Clocks(local)
+    torch.cuda.synchronize(dev)
+    barrier(pg, local if pg is not None and torch.distributed.get_backend() == "nccl" else None)
+    h.stats_reset(time_stages=True)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    st = h.stats()
+    T = ev0.elapsed_time(ev1) / 1e3
+    T = max_over_ranks(pg, T, dev if pg is not None and torch.distributed.get_backend() == "nccl" else None)
+    units = spectrum_cells * args.steps * world
+    value = units / T
+    repeat_ok = bool(np.array_equal(R, R_warm))
+
+    peak, peak_kind = peaks()
+    achieved = st["stage_bytes"] / (st["stage_ms"] / 1e3) / 1e9 if st["stage_ms"] > 0 else None
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_cell_stage_two_mode_32")
+        except Exception:
+            traffic = None
+    roofline = {
+        "kernel": "stage_kernel<float,2,4>",
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+        "traffic": traffic,
+        "algorithmic_bytes_per_cell_stage": ELEM_ACCESSES_PER_CELL_STEP * 4 / 4,
+        "stage_launches": st["stage_launches"],
+        "avg_launch_ms": st["stage_ms"] / max(1, st["stage_launches"]),
+    }
+
+    # end to end through the public API from pinned host memory: every step uploads the
+    # equilibrium (M*P doubles) and reads R back
+    e2e = None
+    if not args.no_e2e:
+        Weq = torch.empty(h.state_shape, dtype=torch.float64, pin_memory=True).numpy()
+        Weq[...] = h.get_equilibrium()
+        torch.cuda.synchronize(dev)
+        barrier(pg, local if pg is not None and torch.distributed.get_backend() == "nccl" else None)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            h.set_equilibrium(Weq)
+            step()
+        torch.cuda.synchronize(dev)
+        Te = time.perf_counter() - t0
+        Te = max_over_ranks(pg, Te, dev if pg is not None and torch.distributed.get_backend() == "nccl" else None)
+        e2e = {"value": spectrum_cells * args.steps * world / Te, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": int(Weq.nbytes), "d2h_bytes_per_step": int(R.nbytes),
+               "spectra_per_s": args.steps * world / Te}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, dt, threads, _ = oracle_sample(wl, 1)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+               "sample": f"1 FP64 RK4 step of one 32^4 x 15-member state ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": "CHFPE cell-updates/s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name + ": 2 coupled anharmonic modes, 32^4 grid, depth 4 "
+                       "(15 members), LL+SL, dt=0.005, R2 on %dx%d (t1,t2) at dtau=0.2, all t1 "
+                       "branches batched" % (nt1, nt2),
+                       "cells_per_state": wl.cells, "cell_updates_per_spectrum": spectrum_cells,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (branch arrays 3 x %.1f GB)" % (
+                           nt1 * wl.cells * 4 / 1e9),
+                       "equilibration": {"steps": eq_steps, "residual": eq_res, "seconds": eq_s}},
+            "spectra_per_s": args.steps * world / T,
+            "roofline": roofline,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": st["kernel_launches"],
+            "repeatable": repeat_ok,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
+def main():
+    args = parse()
+    rank, world, local, pg = dist_setup(args.gpus)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

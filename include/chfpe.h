@@ -1,0 +1,176 @@
+/*
+ * chfpe.h -- C ABI of libchfpe.so: B300 (sm_103a) propagation of the multimode classical
+ * hierarchical Fokker-Planck equations (CHFPE) of Hoshino & Tanimura, arXiv 2509.25840, and the
+ * linear / second-order optical response functions computed from them.
+ *
+ * Method (paper section / equation):
+ *   model      H_sys = sum_s [p_s^2/2m_s + U_s(q_s)] + sum_{s<s'} U_ss'(q_s, q_s')
+ *              U_s = m_s omega_s^2 q^2/2 + g3_s q^3/3! + g4_s q^4/4!          (Eq. "sec: Potenentials";
+ *              the quartic g4 extends the paper's cubic potential in the same convention)
+ *              U_ss' = g2 q_s q_s' + (g_s2s q_s^2 q_s' + g_ss2 q_s q_s'^2)/6  (Eq. "sec: Potential ss'")
+ *   bath       V_s(q) = V_LL q + V_SL q^2/2, Drude spectral density with zeta_s, gamma_s  (Sec. II A,
+ *              Eqs. h_int, drude)
+ *   hierarchy  Eq. HEOM with the Liouvillian of Eq. CL_liouville, Phi (Eq. Phi), Theta (Eq. Theta),
+ *              one auxiliary index per mode, the factor n_s on Theta (Appendix A), truncation at
+ *              n_1 + ... + n_d <= depth
+ *   responses  R1(t)      = integral C  G(t) A^x W_eq                       (Eq. 1Dresponse)
+ *              R2(t2, t1) = integral C  G(t2) B^x G(t1) A^x W_eq            (Eq. 2Dresponse)
+ *              X^x W = sum_s dX/dq_s dW/dp_s on every member                 (Eq. Opticalexc)
+ *              X(q) = sum_s X_s q_s + 1/2 sum_{s,s'} X_ss' q_s q_s'          (Eqs. NLdip, NLpol)
+ *
+ * Discretisation: uniform grid per axis with both end points, 6th-order central differences
+ * (45, -9, 1)/60h with zero values outside the grid, classical RK4 in time.  States hold the
+ * symmetrised members
+ *     g^(n)(q,p) = W^(n)(q,p) exp(+H_sys/2kT) / lambda_n,  lambda_n = prod_s sqrt(n_s! c_s^n_s),
+ *     c_s = zeta_s gamma_s m_s kT,
+ * (the exp(-H/2kT) prefactor of the paper's Appendix A), for which the discrete generator is
+ * antisymmetric minus a non-negative diagonal.  Observables are integral C(q) exp(-H/2kT) g^(0).
+ *
+ * Layout of one state: double or float values, [member][q_1]..[q_d][p_1]..[p_d], p_d fastest;
+ * members ordered by tier |n| then lexicographically ascending in (n_1..n_d).  A batch of states
+ * is [batch][member][...], contiguous.
+ *
+ * Conventions: every call returns a status; chfpe_last_error() gives the calling thread's message
+ * for the last failure.  Handles own all device memory they allocate; callers own every buffer
+ * they pass; the library never frees caller memory.  No exception crosses the ABI.  All calls on
+ * one handle are issued on the handle's stream and are not thread-safe for that handle.
+ */
+#ifndef CHFPE_H
+#define CHFPE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chfpe_handle chfpe_handle;
+
+typedef enum {
+    CHFPE_OK = 0,
+    CHFPE_EINVAL = 1,     /* invalid argument (sizes, pointers, dt above the stability bound)   */
+    CHFPE_ENOMEM = 2,     /* device allocation failed                                           */
+    CHFPE_ECUDA = 3,      /* a CUDA runtime call failed (message has cudaGetErrorString)        */
+    CHFPE_EUNSTABLE = 4,  /* non-finite response or state                                       */
+    CHFPE_ETIMEOUT = 5,   /* a bounded device wait gave up                                      */
+    CHFPE_ESTATE = 6      /* call out of order (e.g. a response before an equilibrium exists)   */
+} chfpe_status;
+
+/* System and bath parameters (Sec. II A).  Index s = 0..nmodes-1; pair terms are read from the
+ * upper triangle (s < s') only. */
+typedef struct {
+    int nmodes;                                    /* d, 1..3                                  */
+    double kT;                                     /* 1/beta                                   */
+    double m[3], omega[3], g3[3], g4[3];
+    double g2[3][3], g_s2s[3][3], g_ss2[3][3];
+    double zeta[3], gamma[3], V_LL[3], V_SL[3];
+} chfpe_model;
+
+/* An optical operator X(q) = sum_s lin[s] q_s + 1/2 sum_{s,s'} quad[s][s'] q_s q_s' (mu or Pi);
+ * only the symmetric part of quad matters. */
+typedef struct {
+    double lin[3];
+    double quad[3][3];
+} chfpe_optical;
+
+/* Uniform grid per axis: nq[s] points on [qmin[s], qmax[s]], np[s] points on [pmin[s], pmax[s]],
+ * end points included; at least 7 points per axis. */
+typedef struct {
+    int nq[3], np[3];
+    double qmin[3], qmax[3], pmin[3], pmax[3];
+} chfpe_grid;
+
+typedef struct {
+    int depth;          /* hierarchy truncation: members with n_1+..+n_d <= depth              */
+    int precision;      /* 32: float state and arithmetic; 64: double (check build)            */
+    double dt;          /* RK4 time step; create fails if dt exceeds the stability bound       */
+    int max_batch;      /* most states propagated together by one launch (response branches)  */
+    void *stream;       /* cudaStream_t to issue work on; NULL = a stream the handle creates   */
+} chfpe_options;
+
+/* Create a handle for one model on one grid.  Validates the structs, builds the coefficient
+ * tables, checks dt * (bound on the generator's spectral radius) <= 2.6 (RK4 stability) and
+ * allocates the state arenas.  *out receives the handle (NULL on failure).
+ * Paper: Sec. IV A (initialisation). */
+chfpe_status chfpe_create(const chfpe_model *model, const chfpe_grid *grid,
+                          const chfpe_options *opts, chfpe_handle **out);
+
+/* Release every device allocation of the handle.  NULL is allowed. */
+void chfpe_destroy(chfpe_handle *h);
+
+/* Equilibrium by propagation (Sec. IV B): g^(0) <- the normalised Boltzmann distribution, other
+ * members 0, then FP64 RK4 steps in blocks of check_every until
+ * max|M g| / max|g| < tol or max_steps steps are taken.  The result, converted to the handle's
+ * precision, becomes the equilibrium that responses start from.  *steps and *residual (either
+ * may be NULL) receive the steps taken and the last residual. */
+chfpe_status chfpe_equilibrate(chfpe_handle *h, long max_steps, double tol, long check_every,
+                               long *steps, double *residual);
+
+/* Equilibrium from the caller: host array of M*P doubles (symmetrised members, layout above). */
+chfpe_status chfpe_set_equilibrium(chfpe_handle *h, const double *host);
+/* Copy the current equilibrium (M*P doubles) to a caller-owned host array. */
+chfpe_status chfpe_get_equilibrium(const chfpe_handle *h, double *host);
+
+/* The working state (one state, M*P doubles): set, read back, or advance by nsteps RK4 steps. */
+chfpe_status chfpe_set_state(chfpe_handle *h, const double *host);
+chfpe_status chfpe_get_state(const chfpe_handle *h, double *host);
+chfpe_status chfpe_propagate(chfpe_handle *h, long nsteps);
+
+/* R1 (Eq. 1Dresponse): R[k] = integral C G(k stride dt) A^x W_eq, k = 0..nt-1, into caller-owned
+ * host memory (nt doubles).  The paper takes C = A. */
+chfpe_status chfpe_response1(chfpe_handle *h, const chfpe_optical *A, const chfpe_optical *C,
+                             int nt, int stride, double *R);
+
+/* R2 (Eq. 2Dresponse): R[i*nt2 + j] = integral C G(j stride dt) B^x G(i stride dt) A^x W_eq,
+ * i = 0..nt1-1 (t1), j = 0..nt2-1 (t2), into caller-owned host memory (nt1*nt2 doubles).  All
+ * t1 branches of a chunk of up to max_batch branches advance together in one batched launch per
+ * RK4 stage.  RTT / TRT / TTR (Sec. V) are the choices of which of A, B, C is Pi. */
+chfpe_status chfpe_response2(chfpe_handle *h, const chfpe_optical *A, const chfpe_optical *B,
+                             const chfpe_optical *C, int nt1, int nt2, int stride, double *R);
+
+/* Save / load the equilibrium (FP64, with a header: grid, depth, members) -- Sec. IV B saves
+ * W_eq to a file and Sec. IV C reads it back. */
+chfpe_status chfpe_save_equilibrium(const chfpe_handle *h, const char *path);
+chfpe_status chfpe_load_equilibrium(chfpe_handle *h, const char *path);
+
+/* Sizes of the handle: members M and points per member P (states are M*P values). */
+chfpe_status chfpe_sizes(const chfpe_handle *h, int *members, long *points);
+
+/* ---- device-buffer entry points (the kernels one by one; buffers are caller-owned device
+ *      memory of the handle's precision, batch states contiguous) ------------------------------ */
+
+/* out = M in (right-hand side of the symmetrised hierarchy) for `batch` states. */
+chfpe_status chfpe_rhs_device(chfpe_handle *h, const void *in, void *out, int batch);
+/* Advance `batch` states in place by nsteps RK4 steps (needs batch <= max_batch). */
+chfpe_status chfpe_rk4_device(chfpe_handle *h, void *states, int batch, long nsteps);
+/* out = X^x in for `batch` states (Eq. Opticalexc, every member). */
+chfpe_status chfpe_insert_device(chfpe_handle *h, const chfpe_optical *X, const void *in,
+                                 void *out, int batch);
+/* R_dev[b] = integral C exp(-H/2kT) g^(0) of state b, FP64 accumulation; R_dev is device memory
+ * of `batch` doubles. */
+chfpe_status chfpe_observe_device(chfpe_handle *h, const chfpe_optical *C, const void *in,
+                                  int batch, double *R_dev);
+
+/* ---- counters for measurement (no counterpart in the paper) ---------------------------------- */
+
+typedef struct {
+    long long kernel_launches;   /* kernels the library launched since the last reset           */
+    long long stage_launches;    /* RK4 stage launches inside timed propagation bursts          */
+    double stage_ms;             /* device time of those bursts: CUDA events on the handle's    */
+                                 /* stream around each burst of back-to-back stage launches      */
+    double stage_bytes;          /* algorithmic bytes of those stages: 11 element accesses per  */
+                                 /* cell and RK4 step (2 + 3 + 3 + 3), times the element size   */
+    double cell_updates;         /* RK4 steps x cells (member x grid point) advanced, all bursts */
+} chfpe_stats;
+
+/* Zero the counters; time_stages != 0 also records CUDA events around every propagation burst
+ * (adds two event records per burst of 4 x stride launches). */
+chfpe_status chfpe_stats_reset(chfpe_handle *h, int time_stages);
+/* Synchronise the handle's stream and read the counters. */
+chfpe_status chfpe_stats_get(chfpe_handle *h, chfpe_stats *out);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *chfpe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHFPE_H */

@@ -1,0 +1,286 @@
+"""Thin ctypes binding of libchfpe.so (include/chfpe.h): argument marshalling only.
+
+Every numerical step runs in the library's CUDA kernels.  Loading fails loudly when the library
+is missing or cannot be opened; there is no CPU fallback.  Device buffers are passed as raw
+pointers (e.g. ``tensor.data_ptr()`` of a contiguous torch CUDA tensor of the handle's dtype).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchfpe.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
+_NAMES = {0: "CHFPE_OK", 1: "CHFPE_EINVAL", 2: "CHFPE_ENOMEM", 3: "CHFPE_ECUDA",
+          4: "CHFPE_EUNSTABLE", 5: "CHFPE_ETIMEOUT", 6: "CHFPE_ESTATE"}
+
+
+class ChfpeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class chfpe_model(ctypes.Structure):
+    _fields_ = [("nmodes", ctypes.c_int), ("kT", ctypes.c_double),
+                ("m", ctypes.c_double * 3), ("omega", ctypes.c_double * 3),
+                ("g3", ctypes.c_double * 3), ("g4", ctypes.c_double * 3),
+                ("g2", (ctypes.c_double * 3) * 3), ("g_s2s", (ctypes.c_double * 3) * 3),
+                ("g_ss2", (ctypes.c_double * 3) * 3),
+                ("zeta", ctypes.c_double * 3), ("gamma", ctypes.c_double * 3),
+                ("V_LL", ctypes.c_double * 3), ("V_SL", ctypes.c_double * 3)]
+
+
+class chfpe_optical(ctypes.Structure):
+    _fields_ = [("lin", ctypes.c_double * 3), ("quad", (ctypes.c_double * 3) * 3)]
+
+
+class chfpe_grid(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_int * 3), ("np", ctypes.c_int * 3),
+                ("qmin", ctypes.c_double * 3), ("qmax", ctypes.c_double * 3),
+                ("pmin", ctypes.c_double * 3), ("pmax", ctypes.c_double * 3)]
+
+
+class chfpe_options(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int), ("precision", ctypes.c_int), ("dt", ctypes.c_double),
+                ("max_batch", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class chfpe_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("stage_launches", ctypes.c_longlong),
+                ("stage_ms", ctypes.c_double), ("stage_bytes", ctypes.c_double),
+                ("cell_updates", ctypes.c_double)]
+
+
+_lib = None
+_DP = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+_H = ctypes.c_void_p
+
+
+def load(path: str = LIB_PATH):
+    """Open libchfpe.so (once).  Raises if it is missing: build it with
+    ``python -m paper_2509_25840_b300.build`` or ``__graft_entry__.build()``."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libchfpe.so not found at {path}; build it first "
+                           "(python -m paper_2509_25840_b300.build)")
+    lib = ctypes.CDLL(path)
+    S = ctypes.c_int
+    sig = {
+        "chfpe_create": ([ctypes.POINTER(chfpe_model), ctypes.POINTER(chfpe_grid),
+                          ctypes.POINTER(chfpe_options), ctypes.POINTER(_H)], S),
+        "chfpe_destroy": ([_H], None),
+        "chfpe_equilibrate": ([_H, ctypes.c_long, ctypes.c_double, ctypes.c_long,
+                               ctypes.POINTER(ctypes.c_long), _DP], S),
+        "chfpe_set_equilibrium": ([_H, _DP], S),
+        "chfpe_get_equilibrium": ([_H, _DP], S),
+        "chfpe_set_state": ([_H, _DP], S),
+        "chfpe_get_state": ([_H, _DP], S),
+        "chfpe_propagate": ([_H, ctypes.c_long], S),
+        "chfpe_response1": ([_H, ctypes.POINTER(chfpe_optical), ctypes.POINTER(chfpe_optical),
+                             ctypes.c_int, ctypes.c_int, _DP], S),
+        "chfpe_response2": ([_H, ctypes.POINTER(chfpe_optical), ctypes.POINTER(chfpe_optical),
+                             ctypes.POINTER(chfpe_optical), ctypes.c_int, ctypes.c_int,
+                             ctypes.c_int, _DP], S),
+        "chfpe_save_equilibrium": ([_H, ctypes.c_char_p], S),
+        "chfpe_load_equilibrium": ([_H, ctypes.c_char_p], S),
+        "chfpe_sizes": ([_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)], S),
+        "chfpe_rhs_device": ([_H, _VP, _VP, ctypes.c_int], S),
+        "chfpe_rk4_device": ([_H, _VP, ctypes.c_int, ctypes.c_long], S),
+        "chfpe_insert_device": ([_H, ctypes.POINTER(chfpe_optical), _VP, _VP, ctypes.c_int], S),
+        "chfpe_observe_device": ([_H, ctypes.POINTER(chfpe_optical), _VP, ctypes.c_int, _VP], S),
+        "chfpe_stats_reset": ([_H, ctypes.c_int], S),
+        "chfpe_stats_get": ([_H, ctypes.POINTER(chfpe_stats)], S),
+        "chfpe_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().chfpe_last_error().decode()
+
+
+def _check(status: int):
+    if status != OK:
+        raise ChfpeError(status, last_error())
+
+
+def _fill(arr, vals, n=3):
+    vals = list(vals) + [0] * n
+    for i in range(n):
+        arr[i] = vals[i]
+
+
+def make_model(model: "inputs.Model") -> chfpe_model:
+    m = chfpe_model()
+    m.nmodes = int(model.nmodes)
+    m.kT = float(model.kT)
+    for name in ("m", "omega", "g3", "g4", "zeta", "gamma", "V_LL", "V_SL"):
+        _fill(getattr(m, name), [float(x) for x in getattr(model, name)])
+    for name in ("g2", "g_s2s", "g_ss2"):
+        src = np.asarray(getattr(model, name), dtype=np.float64)
+        dst = getattr(m, name)
+        for i in range(3):
+            for j in range(3):
+                dst[i][j] = float(src[i, j]) if i < src.shape[0] and j < src.shape[1] else 0.0
+    return m
+
+
+def make_grid(grid: "inputs.Grid") -> chfpe_grid:
+    g = chfpe_grid()
+    _fill(g.nq, [int(x) for x in grid.nq])
+    _fill(g.np, [int(x) for x in grid.np])
+    for name in ("qmin", "qmax", "pmin", "pmax"):
+        _fill(getattr(g, name), [float(x) for x in getattr(grid, name)])
+    return g
+
+
+def make_optical(X: "inputs.Optical") -> chfpe_optical:
+    o = chfpe_optical()
+    _fill(o.lin, [float(x) for x in X.lin])
+    q = np.asarray(X.quad, dtype=np.float64)
+    for i in range(3):
+        for j in range(3):
+            o.quad[i][j] = float(q[i, j]) if i < q.shape[0] and j < q.shape[1] else 0.0
+    return o
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+class Handle:
+    """One model on one grid: owns the device arenas of libchfpe."""
+
+    def __init__(self, model, grid, depth: int, dt: float, precision: int = 32,
+                 max_batch: int = 1, stream: int | None = None):
+        lib = load()
+        self._m, self._g = make_model(model), make_grid(grid)
+        self._o = chfpe_options(depth=int(depth), precision=int(precision), dt=float(dt),
+                                max_batch=int(max_batch), stream=stream)
+        h = _H()
+        _check(lib.chfpe_create(ctypes.byref(self._m), ctypes.byref(self._g),
+                                ctypes.byref(self._o), ctypes.byref(h)))
+        self._h = h
+        M, P = ctypes.c_int(), ctypes.c_long()
+        _check(lib.chfpe_sizes(h, ctypes.byref(M), ctypes.byref(P)))
+        self.members, self.points = M.value, P.value
+        self.shape = tuple(grid.nq) + tuple(grid.np)
+        self.precision = int(precision)
+        self.max_batch = int(max_batch)
+
+    # -- lifetime -------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().chfpe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def state_shape(self):
+        return (self.members,) + self.shape
+
+    def _host(self, a) -> np.ndarray:
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.size != self.members * self.points:
+            raise ValueError(f"state has {a.size} values, expected {self.members * self.points}")
+        return a
+
+    # -- equilibrium and states -------------------------------------------------------------
+    def equilibrate(self, max_steps: int, tol: float, check_every: int = 100):
+        steps, res = ctypes.c_long(), ctypes.c_double()
+        _check(load().chfpe_equilibrate(self._h, int(max_steps), float(tol), int(check_every),
+                                        ctypes.byref(steps), ctypes.byref(res)))
+        return steps.value, res.value
+
+    def set_equilibrium(self, W):
+        a = self._host(W)
+        _check(load().chfpe_set_equilibrium(self._h, _dptr(a)))
+
+    def get_equilibrium(self) -> np.ndarray:
+        out = np.empty(self.state_shape)
+        _check(load().chfpe_get_equilibrium(self._h, _dptr(out)))
+        return out
+
+    def set_state(self, W):
+        a = self._host(W)
+        _check(load().chfpe_set_state(self._h, _dptr(a)))
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty(self.state_shape)
+        _check(load().chfpe_get_state(self._h, _dptr(out)))
+        return out
+
+    def propagate(self, nsteps: int):
+        _check(load().chfpe_propagate(self._h, int(nsteps)))
+
+    def save_equilibrium(self, path: str):
+        _check(load().chfpe_save_equilibrium(self._h, os.fsencode(path)))
+
+    def load_equilibrium(self, path: str):
+        _check(load().chfpe_load_equilibrium(self._h, os.fsencode(path)))
+
+    # -- responses ----------------------------------------------------------------------------
+    def response1(self, A, C, nt: int, stride: int, out: np.ndarray | None = None) -> np.ndarray:
+        R = np.empty(nt) if out is None else out
+        a, c = make_optical(A), make_optical(C)
+        _check(load().chfpe_response1(self._h, ctypes.byref(a), ctypes.byref(c), int(nt),
+                                      int(stride), _dptr(R)))
+        return R
+
+    def response2(self, A, B, C, nt1: int, nt2: int, stride: int,
+                  out: np.ndarray | None = None) -> np.ndarray:
+        R = np.empty((nt1, nt2)) if out is None else out
+        a, b, c = make_optical(A), make_optical(B), make_optical(C)
+        _check(load().chfpe_response2(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                      int(nt1), int(nt2), int(stride), _dptr(R)))
+        return R
+
+    # -- device buffers -------------------------------------------------------------------------
+    def rhs_device(self, in_ptr: int, out_ptr: int, batch: int = 1):
+        _check(load().chfpe_rhs_device(self._h, in_ptr, out_ptr, int(batch)))
+
+    def rk4_device(self, ptr: int, batch: int, nsteps: int):
+        _check(load().chfpe_rk4_device(self._h, ptr, int(batch), int(nsteps)))
+
+    def insert_device(self, X, in_ptr: int, out_ptr: int, batch: int = 1):
+        x = make_optical(X)
+        _check(load().chfpe_insert_device(self._h, ctypes.byref(x), in_ptr, out_ptr, int(batch)))
+
+    def observe_device(self, C, in_ptr: int, batch: int, R_ptr: int):
+        c = make_optical(C)
+        _check(load().chfpe_observe_device(self._h, ctypes.byref(c), in_ptr, int(batch), R_ptr))
+
+    # -- counters ---------------------------------------------------------------------------------
+    def stats_reset(self, time_stages: bool = False):
+        _check(load().chfpe_stats_reset(self._h, int(bool(time_stages))))
+
+    def stats(self) -> dict:
+        st = chfpe_stats()
+        _check(load().chfpe_stats_get(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in chfpe_stats._fields_}

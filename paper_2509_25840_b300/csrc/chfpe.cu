@@ -1,0 +1,963 @@
+// chfpe.cu -- libchfpe.so: handle, coefficient set-up, RK4 driver and response drivers of the
+// CHFPE hot path (declared in include/chfpe.h).  Everything numerical runs in the kernels of
+// kernels.cuh; host code here validates, sizes, launches and copies.
+#include "../../include/chfpe.h"
+#include "kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace chfpe;
+
+// ------------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------------
+
+static thread_local std::string g_err;
+
+static chfpe_status fail(chfpe_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(CHFPE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+extern "C" const char *chfpe_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------------------------------
+// handle
+// ------------------------------------------------------------------------------------------
+
+static int max_depth_for(int d) { return d == 1 ? 8 : (d == 2 ? 5 : 3); }
+
+struct chfpe_handle {
+    chfpe_model model;
+    chfpe_grid grid;
+    chfpe_options opts;
+    int d = 0, depth = 0, M = 0, prec = 32;
+    int P = 0, Pp = 0, NQ = 0;
+    int n[6] = {0}, st[6] = {0};
+    double lo[6] = {0}, h[6] = {0};
+    double dt = 0.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t esize = 4;           // bytes per state value
+    long long state = 0;        // values per state
+
+    // coefficient tables (device)
+    double *U_d = nullptr;      // [NQ] U(q)
+    double *F_d = nullptr;      // [d][NQ] dU/dq_s / (60 h_ps)
+    float *F_f = nullptr;
+    double *wp = nullptr;       // [3][wp_ld] exp(-p^2 / 4 m kT)
+    int wp_ld = 0;
+    double *CWq = nullptr;      // [NQ] C(q) exp(-U/2kT), per observe call
+    int *np_d = nullptr;
+    double *plo_d = nullptr, *ph_d = nullptr, *inv2m_d = nullptr;
+
+    // state arenas (precision of the handle)
+    void *cy = nullptr, *ca = nullptr, *cb = nullptr;      // chain / working state (1 state)
+    void *by = nullptr, *ba = nullptr, *bb = nullptr;      // branches (max_batch states)
+    void *eq = nullptr;                                    // equilibrium (1 state)
+    bool have_eq = false, have_state = false;
+    double *stage64 = nullptr;                             // FP64 staging (1 state)
+    double *partial = nullptr;                             // reduction partials
+    int partial_cap = 0;
+    double *dR = nullptr;                                  // device response buffer
+    size_t dR_cap = 0;
+
+    // measurement counters
+    long long launches = 0, stage_launches = 0;
+    double stage_bytes = 0.0, cell_updates = 0.0;
+    bool time_stages = false;
+    std::vector<cudaEvent_t> ev;        // pairs (start, stop) of timed bursts
+    size_t ev_used = 0;
+};
+
+template <typename T>
+static StageArgs<T> stage_args(const chfpe_handle *h) {
+    StageArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.state = h->state;
+    a.P = h->P;
+    for (int i = 0; i < 6; ++i) { a.n[i] = h->n[i]; a.st[i] = h->st[i]; }
+    a.Pp = h->Pp;
+    a.NQ = h->NQ;
+    if (sizeof(T) == 8) a.F = (const T *)h->F_d; else a.F = (const T *)h->F_f;
+    const chfpe_model &m = h->model;
+    for (int s = 0; s < h->d; ++s) {
+        const double hq = h->h[s], hp = h->h[h->d + s];
+        a.qlo[s] = (T)h->lo[s];
+        a.qh[s] = (T)hq;
+        a.plo[s] = (T)h->lo[h->d + s];
+        a.ph[s] = (T)hp;
+        a.vq[s] = (T)(1.0 / (m.m[s] * 60.0 * hq));
+        a.inv60hp[s] = (T)(1.0 / (60.0 * hp));
+        a.kappa[s] = (T)(1.0 / (2.0 * m.m[s] * m.kT));
+        a.VLL[s] = (T)m.V_LL[s];
+        a.VSL[s] = (T)m.V_SL[s];
+        a.gam[s] = (T)m.gamma[s];
+        const double c = m.zeta[s] * m.gamma[s] * m.m[s] * m.kT;
+        for (int k = 0; k < kMaxDepth + 2; ++k) a.link[s][k] = (T)std::sqrt(k * c);
+    }
+    return a;
+}
+
+template <typename T, int D, int DEPTH>
+static void launch_stage_t(const StageArgs<T> &a, int batch, cudaStream_t s) {
+    dim3 grid((a.P + 255) / 256, batch);
+    stage_kernel<T, D, DEPTH><<<grid, 256, 0, s>>>(a);
+}
+
+template <typename T>
+static bool launch_stage(const chfpe_handle *h, const StageArgs<T> &a, int batch) {
+    cudaStream_t s = h->stream;
+#define CASE(D_, K_) \
+    case (D_ * 16 + K_): launch_stage_t<T, D_, K_>(a, batch, s); return true;
+    switch (h->d * 16 + h->depth) {
+        CASE(1, 0) CASE(1, 1) CASE(1, 2) CASE(1, 3) CASE(1, 4) CASE(1, 5) CASE(1, 6) CASE(1, 7)
+        CASE(1, 8)
+        CASE(2, 0) CASE(2, 1) CASE(2, 2) CASE(2, 3) CASE(2, 4) CASE(2, 5)
+        CASE(3, 0) CASE(3, 1) CASE(3, 2) CASE(3, 3)
+        default: return false;
+    }
+#undef CASE
+}
+
+// one stage over `batch` states: out = y + c * M in   (y == nullptr: out = c * M in)
+template <typename T>
+static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *out, double c,
+                          int batch) {
+    StageArgs<T> a = stage_args<T>(h);
+    a.in = (const T *)in;
+    a.y = (const T *)y;
+    a.out = (T *)out;
+    a.c = (T)c;
+    if (!launch_stage<T>(h, a, batch)) return fail(CHFPE_EINVAL, "unsupported (d, depth)");
+    CK(cudaGetLastError());
+    ++h->launches;
+    return CHFPE_OK;
+}
+
+static chfpe_status burst_event(chfpe_handle *h) {
+    if (h->ev_used == h->ev.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->ev.push_back(e);
+    }
+    CK(cudaEventRecord(h->ev[h->ev_used++], h->stream));
+    return CHFPE_OK;
+}
+
+// RK4 for a linear autonomous system in Horner form: y <- R4(dt M) y with
+//   z1 = y + dt/4 M y, z2 = y + dt/3 M z1, z3 = y + dt/2 M z2, y <- y + dt M z3
+// (identical to the classical k1..k4 form in exact arithmetic; 11 element accesses per cell
+// and step instead of 16, the last stage in place).
+template <typename T>
+static chfpe_status rk4(chfpe_handle *h, void *y, void *za, void *zb, int batch, long nsteps) {
+    const double dt = h->dt;
+    chfpe_status st;
+    if (nsteps <= 0) return CHFPE_OK;
+    if (h->time_stages && (st = burst_event(h))) return st;
+    for (long s = 0; s < nsteps; ++s) {
+        if ((st = stage<T>(h, y, y, za, dt / 4.0, batch))) return st;
+        if ((st = stage<T>(h, za, y, zb, dt / 3.0, batch))) return st;
+        if ((st = stage<T>(h, zb, y, za, dt / 2.0, batch))) return st;
+        if ((st = stage<T>(h, za, y, y, dt, batch))) return st;
+    }
+    if (h->time_stages && (st = burst_event(h))) return st;
+    const double cells = (double)nsteps * batch * (double)h->state;
+    h->cell_updates += cells;
+    if (h->time_stages) {
+        h->stage_launches += 4 * nsteps;
+        h->stage_bytes += cells * 11.0 * sizeof(T);
+    }
+    return CHFPE_OK;
+}
+
+static chfpe_status rk4_any(chfpe_handle *h, void *y, void *za, void *zb, int batch, long n) {
+    return h->prec == 64 ? rk4<double>(h, y, za, zb, batch, n) : rk4<float>(h, y, za, zb, batch, n);
+}
+
+// ------------------------------------------------------------------------------------------
+// coefficient set-up kernels (run once per handle / per observable)
+// ------------------------------------------------------------------------------------------
+
+struct ModelDev {
+    int d;
+    double kT, m[3], w2[3], g3[3], g4[3], g2[3][3], gs2s[3][3], gss2[3][3];
+    int nq[3];
+    double qlo[3], qh[3], inv60hp[3];
+};
+
+__device__ static double dev_potential(const ModelDev &md, const double *q) {
+    double U = 0.0;
+    for (int s = 0; s < md.d; ++s) {
+        const double x = q[s];
+        U += 0.5 * md.m[s] * md.w2[s] * x * x + md.g3[s] * x * x * x * (1.0 / 6.0) +
+             md.g4[s] * x * x * x * x * (1.0 / 24.0);
+    }
+    for (int a = 0; a < md.d; ++a)
+        for (int b = a + 1; b < md.d; ++b)
+            U += md.g2[a][b] * q[a] * q[b] +
+                 (md.gs2s[a][b] * q[a] * q[a] * q[b] + md.gss2[a][b] * q[a] * q[b] * q[b]) *
+                     (1.0 / 6.0);
+    return U;
+}
+
+__device__ static double dev_force(const ModelDev &md, const double *q, int s) {
+    const double x = q[s];
+    double F = md.m[s] * md.w2[s] * x + 0.5 * md.g3[s] * x * x + md.g4[s] * x * x * x * (1.0 / 6.0);
+    for (int b = 0; b < md.d; ++b) {
+        if (b > s)
+            F += md.g2[s][b] * q[b] + (2.0 * md.gs2s[s][b] * x * q[b] + md.gss2[s][b] * q[b] * q[b]) * (1.0 / 6.0);
+        else if (b < s)
+            F += md.g2[b][s] * q[b] + (md.gs2s[b][s] * q[b] * q[b] + 2.0 * md.gss2[b][s] * q[b] * x) * (1.0 / 6.0);
+    }
+    return F;
+}
+
+__device__ static void dev_qpoint(const ModelDev &md, int qlin, double *q) {
+    int r = qlin;
+    for (int s = md.d - 1; s >= 0; --s) {
+        const int i = r % md.nq[s];
+        r /= md.nq[s];
+        q[s] = md.qlo[s] + i * md.qh[s];
+    }
+}
+
+__global__ static void setup_fields_kernel(ModelDev md, int NQ, double *U, double *F, float *Ff) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NQ) return;
+    double q[3] = {0, 0, 0};
+    dev_qpoint(md, i, q);
+    U[i] = dev_potential(md, q);
+    for (int s = 0; s < md.d; ++s) {
+        const double f = dev_force(md, q, s) * md.inv60hp[s];
+        F[s * NQ + i] = f;
+        Ff[s * NQ + i] = (float)f;
+    }
+}
+
+__global__ static void setup_wp_kernel(int d, const int *np, const double *plo, const double *ph,
+                                       const double *inv2m, double inv2kT, double *wp, int ld) {
+    const int s = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d || i >= np[s]) return;
+    const double p = plo[s] + i * ph[s];
+    // exp(-p^2 / (4 m kT)) = exp(-(p^2 / 2m) / 2kT)
+    wp[s * ld + i] = exp(-p * p * inv2m[s] * inv2kT);
+}
+
+struct OpticalDev {
+    double lin[3], quad[3][3];
+};
+
+__global__ static void setup_cwq_kernel(ModelDev md, OpticalDev X, int NQ, const double *U,
+                                        double inv2kT, double *CWq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NQ) return;
+    double q[3] = {0, 0, 0};
+    dev_qpoint(md, i, q);
+    double c = 0.0;
+    for (int s = 0; s < md.d; ++s) c += X.lin[s] * q[s];
+    for (int a = 0; a < md.d; ++a)
+        for (int b = 0; b < md.d; ++b) c += 0.5 * X.quad[a][b] * q[a] * q[b];
+    CWq[i] = c * exp(-U[i] * inv2kT);
+}
+
+static ModelDev model_dev(const chfpe_handle *h) {
+    ModelDev md;
+    memset(&md, 0, sizeof(md));
+    const chfpe_model &m = h->model;
+    md.d = h->d;
+    md.kT = m.kT;
+    for (int s = 0; s < 3; ++s) {
+        md.m[s] = m.m[s];
+        md.w2[s] = m.omega[s] * m.omega[s];
+        md.g3[s] = m.g3[s];
+        md.g4[s] = m.g4[s];
+        for (int b = 0; b < 3; ++b) {
+            md.g2[s][b] = m.g2[s][b];
+            md.gs2s[s][b] = m.g_s2s[s][b];
+            md.gss2[s][b] = m.g_ss2[s][b];
+        }
+    }
+    for (int s = 0; s < h->d; ++s) {
+        md.nq[s] = h->n[s];
+        md.qlo[s] = h->lo[s];
+        md.qh[s] = h->h[s];
+        md.inv60hp[s] = 1.0 / (60.0 * h->h[h->d + s]);
+    }
+    return md;
+}
+
+// ------------------------------------------------------------------------------------------
+// observation: out[j * out_stride] = integral C exp(-H/2kT) g^(0) of state j
+// ------------------------------------------------------------------------------------------
+
+static chfpe_status set_observable(chfpe_handle *h, const chfpe_optical *C) {
+    OpticalDev X;
+    for (int s = 0; s < 3; ++s) {
+        X.lin[s] = C->lin[s];
+        for (int b = 0; b < 3; ++b) X.quad[s][b] = C->quad[s][b];
+    }
+    setup_cwq_kernel<<<(h->NQ + 127) / 128, 128, 0, h->stream>>>(model_dev(h), X, h->NQ, h->U_d,
+                                                                  0.5 / h->model.kT, h->CWq);
+    CK(cudaGetLastError());
+    ++h->launches;
+    return CHFPE_OK;
+}
+
+static int observe_blocks(const chfpe_handle *h) {
+    int nblk = (h->P + 1023) / 1024;
+    if (nblk > 512) nblk = 512;
+    return nblk < 1 ? 1 : nblk;
+}
+
+static chfpe_status observe(chfpe_handle *h, const void *states, int batch, double *out,
+                            long long out_stride) {
+    const int nblk = observe_blocks(h);
+    if ((long long)nblk * batch > h->partial_cap) return fail(CHFPE_EINVAL, "batch too large for reduction scratch");
+    ObserveArgs a;
+    memset(&a, 0, sizeof(a));
+    a.in = states;
+    a.state = h->state;
+    a.P = h->P;
+    a.Pp = h->Pp;
+    a.d = h->d;
+    for (int s = 0; s < h->d; ++s) a.np[s] = h->n[h->d + s];
+    a.CWq = h->CWq;
+    a.wp = h->wp;
+    a.wp_ld = h->wp_ld;
+    a.partial = h->partial;
+    a.nblk = nblk;
+    dim3 grid(nblk, batch);
+    if (h->prec == 64)
+        observe_partial_kernel<double, 256><<<grid, 256, 0, h->stream>>>(a);
+    else
+        observe_partial_kernel<float, 256><<<grid, 256, 0, h->stream>>>(a);
+    CK(cudaGetLastError());
+    double vol = 1.0;
+    for (int ax = 0; ax < 2 * h->d; ++ax) vol *= h->h[ax];
+    observe_finish_kernel<<<batch, 32, 0, h->stream>>>(h->partial, nblk, batch, vol, out, out_stride);
+    CK(cudaGetLastError());
+    h->launches += 2;
+    return CHFPE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// insertion
+// ------------------------------------------------------------------------------------------
+
+template <typename T>
+static chfpe_status insert_t(chfpe_handle *h, const chfpe_optical *X, const void *in,
+                             long long in_state, void *out, int batch) {
+    InsertArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.in = (const T *)in;
+    a.out = (T *)out;
+    a.in_state = in_state;
+    a.out_state = h->state;
+    a.P = h->P;
+    a.M = h->M;
+    a.d = h->d;
+    for (int i = 0; i < 6; ++i) { a.n[i] = h->n[i]; a.st[i] = h->st[i]; }
+    for (int s = 0; s < h->d; ++s) {
+        a.qlo[s] = (T)h->lo[s];
+        a.qh[s] = (T)h->h[s];
+        a.plo[s] = (T)h->lo[h->d + s];
+        a.ph[s] = (T)h->h[h->d + s];
+        a.lin[s] = (T)X->lin[s];
+        for (int b = 0; b < h->d; ++b) a.quad[s][b] = (T)(0.5 * (X->quad[s][b] + X->quad[b][s]));
+        a.inv60hp[s] = (T)(1.0 / (60.0 * h->h[h->d + s]));
+        a.kappa[s] = (T)(1.0 / (2.0 * h->model.m[s] * h->model.kT));
+    }
+    dim3 grid((h->P + 255) / 256, batch);
+    insert_kernel<T><<<grid, 256, 0, h->stream>>>(a);
+    CK(cudaGetLastError());
+    ++h->launches;
+    return CHFPE_OK;
+}
+
+static chfpe_status insert(chfpe_handle *h, const chfpe_optical *X, const void *in,
+                           long long in_state, void *out, int batch) {
+    return h->prec == 64 ? insert_t<double>(h, X, in, in_state, out, batch)
+                         : insert_t<float>(h, X, in, in_state, out, batch);
+}
+
+// ------------------------------------------------------------------------------------------
+// validation and the stability bound
+// ------------------------------------------------------------------------------------------
+
+static bool is_fin(double x) { return std::isfinite(x); }
+
+// Upper bound on the spectral radius of the discrete generator: the stencil's largest
+// modified wavenumber is K/h with K = max |45 sin t - 9 sin 2t + sin 3t| / 30 < 1.59; the
+// Liouvillian contributes max|p|/m K/h_q + max|dU/dq| K/h_p per mode, each of the (at most two)
+// hierarchy links of a member sqrt(depth c) max|V'| (K/h_p + max|p|/2mkT), the damping depth
+// max gamma.  RK4 is stable for |dt lambda| <= 2.78 on both axes; the bound must stay below 2.6.
+static double spectral_bound(const chfpe_handle *h) {
+    const double K = 1.59;
+    const chfpe_model &m = h->model;
+    double rho = 0.0, gmax = 0.0;
+    // max |dU/dq_s| over the q-grid corners and axes (U is a polynomial of degree <= 4; sample
+    // every q node on the host: NQ is small)
+    std::vector<double> Fmax(h->d, 0.0);
+    std::vector<int> qi(h->d, 0);
+    for (int lin = 0; lin < h->NQ; ++lin) {
+        int r = lin;
+        double q[3] = {0, 0, 0};
+        for (int s = h->d - 1; s >= 0; --s) { q[s] = h->lo[s] + (r % h->n[s]) * h->h[s]; r /= h->n[s]; }
+        for (int s = 0; s < h->d; ++s) {
+            double F = m.m[s] * m.omega[s] * m.omega[s] * q[s] + 0.5 * m.g3[s] * q[s] * q[s] +
+                       m.g4[s] * q[s] * q[s] * q[s] / 6.0;
+            for (int b = 0; b < h->d; ++b) {
+                if (b > s) F += m.g2[s][b] * q[b] + (2 * m.g_s2s[s][b] * q[s] * q[b] + m.g_ss2[s][b] * q[b] * q[b]) / 6.0;
+                if (b < s) F += m.g2[b][s] * q[b] + (m.g_s2s[b][s] * q[b] * q[b] + 2 * m.g_ss2[b][s] * q[b] * q[s]) / 6.0;
+            }
+            if (std::fabs(F) > Fmax[s]) Fmax[s] = std::fabs(F);
+        }
+    }
+    for (int s = 0; s < h->d; ++s) {
+        const double hq = h->h[s], hp = h->h[h->d + s];
+        const double pmax = std::fmax(std::fabs(h->lo[h->d + s]), std::fabs(h->lo[h->d + s] + (h->n[h->d + s] - 1) * hp));
+        const double qmax = std::fmax(std::fabs(h->lo[s]), std::fabs(h->lo[s] + (h->n[s] - 1) * hq));
+        const double Vmax = std::fabs(m.V_LL[s]) + std::fabs(m.V_SL[s]) * qmax;
+        const double c = m.zeta[s] * m.gamma[s] * m.m[s] * m.kT;
+        rho += pmax / m.m[s] * K / hq + Fmax[s] * K / hp;
+        rho += 2.0 * std::sqrt(h->depth * c) * Vmax * (K / hp + pmax / (2.0 * m.m[s] * m.kT));
+        gmax = std::fmax(gmax, m.gamma[s]);
+    }
+    return rho + h->depth * gmax;
+}
+
+static chfpe_status validate(const chfpe_model *m, const chfpe_grid *g, const chfpe_options *o) {
+    if (!m || !g || !o) return fail(CHFPE_EINVAL, "null model, grid or options");
+    if (m->nmodes < 1 || m->nmodes > 3) return fail(CHFPE_EINVAL, "nmodes must be 1, 2 or 3");
+    if (!(m->kT > 0) || !is_fin(m->kT)) return fail(CHFPE_EINVAL, "kT must be positive");
+    for (int s = 0; s < m->nmodes; ++s) {
+        if (!(m->m[s] > 0) || !is_fin(m->m[s])) return fail(CHFPE_EINVAL, "masses must be positive");
+        if (m->zeta[s] < 0 || m->gamma[s] < 0) return fail(CHFPE_EINVAL, "zeta, gamma must be >= 0");
+        if (g->nq[s] < 7 || g->np[s] < 7) return fail(CHFPE_EINVAL, "at least 7 points per axis");
+        if (!(g->qmax[s] > g->qmin[s]) || !(g->pmax[s] > g->pmin[s]))
+            return fail(CHFPE_EINVAL, "grid bounds must satisfy min < max");
+    }
+    if (o->depth < 0 || o->depth > max_depth_for(m->nmodes))
+        return fail(CHFPE_EINVAL, "depth out of range (d=1: <=8, d=2: <=5, d=3: <=3)");
+    if (o->precision != 32 && o->precision != 64) return fail(CHFPE_EINVAL, "precision must be 32 or 64");
+    if (!(o->dt > 0) || !is_fin(o->dt)) return fail(CHFPE_EINVAL, "dt must be positive");
+    if (o->max_batch < 1 || o->max_batch > 65535) return fail(CHFPE_EINVAL, "max_batch must be in 1..65535");
+    long long P = 1;
+    for (int s = 0; s < m->nmodes; ++s) P *= (long long)g->nq[s] * g->np[s];
+    const long long M = member_count(m->nmodes, o->depth);
+    if (P * M >= (1LL << 31)) return fail(CHFPE_EINVAL, "state too large (members * points >= 2^31)");
+    return CHFPE_OK;
+}
+
+template <typename T>
+static T *dalloc(size_t n, chfpe_status *st) {
+    void *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *st = fail(CHFPE_ENOMEM, std::string("cudaMalloc(") + std::to_string(n * sizeof(T)) +
+                                    " bytes): " + cudaGetErrorString(e));
+        return nullptr;
+    }
+    return (T *)p;
+}
+
+extern "C" void chfpe_destroy(chfpe_handle *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    void *ptrs[] = {h->U_d, h->F_d, h->F_f, h->wp, h->CWq, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
+                    h->cy, h->ca, h->cb, h->by, h->ba, h->bb, h->eq, h->stage64, h->partial, h->dR};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+extern "C" chfpe_status chfpe_create(const chfpe_model *model, const chfpe_grid *grid,
+                                     const chfpe_options *opts, chfpe_handle **out) {
+    if (!out) return fail(CHFPE_EINVAL, "out is null");
+    *out = nullptr;
+    chfpe_status st = validate(model, grid, opts);
+    if (st) return st;
+    chfpe_handle *h = new chfpe_handle();
+    h->model = *model;
+    h->grid = *grid;
+    h->opts = *opts;
+    h->d = model->nmodes;
+    h->depth = opts->depth;
+    h->M = member_count(h->d, h->depth);
+    h->prec = opts->precision;
+    h->esize = h->prec == 64 ? 8 : 4;
+    h->dt = opts->dt;
+    const int d = h->d;
+    for (int s = 0; s < d; ++s) {
+        h->n[s] = grid->nq[s];
+        h->n[d + s] = grid->np[s];
+        h->lo[s] = grid->qmin[s];
+        h->lo[d + s] = grid->pmin[s];
+        h->h[s] = (grid->qmax[s] - grid->qmin[s]) / (grid->nq[s] - 1);
+        h->h[d + s] = (grid->pmax[s] - grid->pmin[s]) / (grid->np[s] - 1);
+    }
+    h->st[2 * d - 1] = 1;
+    for (int ax = 2 * d - 2; ax >= 0; --ax) h->st[ax] = h->st[ax + 1] * h->n[ax + 1];
+    h->P = h->st[0] * h->n[0];
+    h->Pp = 1;
+    h->NQ = 1;
+    for (int s = 0; s < d; ++s) { h->Pp *= h->n[d + s]; h->NQ *= h->n[s]; }
+    h->state = (long long)h->M * h->P;
+
+    const double rho = spectral_bound(h);
+    if (h->dt * rho > 2.6) {
+        char buf[256];
+        snprintf(buf, sizeof buf, "dt = %g exceeds the RK4 stability bound 2.6 / %g = %g", h->dt,
+                 rho, 2.6 / rho);
+        delete h;
+        return fail(CHFPE_EINVAL, buf);
+    }
+
+    if (opts->stream) {
+        h->stream = (cudaStream_t)opts->stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete h; return fail(CHFPE_ECUDA, cudaGetErrorString(e)); }
+        h->own_stream = true;
+    }
+
+    st = CHFPE_OK;
+    const size_t sb = (size_t)h->state;
+    h->U_d = dalloc<double>(h->NQ, &st);
+    h->F_d = dalloc<double>((size_t)d * h->NQ, &st);
+    h->F_f = dalloc<float>((size_t)d * h->NQ, &st);
+    h->CWq = dalloc<double>(h->NQ, &st);
+    h->wp_ld = 1;
+    for (int s = 0; s < d; ++s) h->wp_ld = std::max(h->wp_ld, h->n[d + s]);
+    h->wp = dalloc<double>((size_t)3 * h->wp_ld, &st);
+    h->np_d = dalloc<int>(3, &st);
+    h->plo_d = dalloc<double>(3, &st);
+    h->ph_d = dalloc<double>(3, &st);
+    h->inv2m_d = dalloc<double>(3, &st);
+    h->partial_cap = observe_blocks(h) * std::max(opts->max_batch, 1);
+    if (h->partial_cap < 4096) h->partial_cap = 4096;
+    h->partial = dalloc<double>(h->partial_cap, &st);
+    void **arenas[] = {&h->cy, &h->ca, &h->cb, &h->eq};
+    for (void **p : arenas) if (!st) *p = (void *)dalloc<char>(sb * h->esize, &st);
+    void **barenas[] = {&h->by, &h->ba, &h->bb};
+    for (void **p : barenas) if (!st) *p = (void *)dalloc<char>(sb * h->esize * opts->max_batch, &st);
+    if (st) { chfpe_destroy(h); return st; }
+
+    // coefficient tables
+    int npv[3] = {1, 1, 1};
+    double plo[3] = {0, 0, 0}, ph[3] = {0, 0, 0}, inv2m[3] = {0, 0, 0};
+    for (int s = 0; s < d; ++s) {
+        npv[s] = h->n[d + s];
+        plo[s] = h->lo[d + s];
+        ph[s] = h->h[d + s];
+        inv2m[s] = 0.5 / model->m[s];
+    }
+    cudaError_t e = cudaSuccess;
+    if (!e) e = cudaMemcpyAsync(h->np_d, npv, sizeof npv, cudaMemcpyHostToDevice, h->stream);
+    if (!e) e = cudaMemcpyAsync(h->plo_d, plo, sizeof plo, cudaMemcpyHostToDevice, h->stream);
+    if (!e) e = cudaMemcpyAsync(h->ph_d, ph, sizeof ph, cudaMemcpyHostToDevice, h->stream);
+    if (!e) e = cudaMemcpyAsync(h->inv2m_d, inv2m, sizeof inv2m, cudaMemcpyHostToDevice, h->stream);
+    if (e) { chfpe_destroy(h); return fail(CHFPE_ECUDA, cudaGetErrorString(e)); }
+    setup_fields_kernel<<<(h->NQ + 127) / 128, 128, 0, h->stream>>>(model_dev(h), h->NQ, h->U_d,
+                                                                     h->F_d, h->F_f);
+    dim3 gw((h->wp_ld + 127) / 128, d);
+    setup_wp_kernel<<<gw, 128, 0, h->stream>>>(d, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
+                                               0.5 / model->kT, h->wp, h->wp_ld);
+    e = cudaGetLastError();
+    if (!e) e = cudaStreamSynchronize(h->stream);
+    if (e) { chfpe_destroy(h); return fail(CHFPE_ECUDA, cudaGetErrorString(e)); }
+    *out = h;
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_sizes(const chfpe_handle *h, int *members, long *points) {
+    if (!h) return fail(CHFPE_EINVAL, "null handle");
+    if (members) *members = h->M;
+    if (points) *points = h->P;
+    return CHFPE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// host <-> device state copies (FP64 on the host, handle precision on the device)
+// ------------------------------------------------------------------------------------------
+
+static chfpe_status ensure_stage64(chfpe_handle *h) {
+    if (h->stage64) return CHFPE_OK;
+    chfpe_status st = CHFPE_OK;
+    h->stage64 = dalloc<double>((size_t)h->state, &st);
+    return st;
+}
+
+static chfpe_status upload(chfpe_handle *h, const double *host, void *dst) {
+    if (!host) return fail(CHFPE_EINVAL, "null host pointer");
+    const size_t n = (size_t)h->state;
+    if (h->prec == 64) {
+        CK(cudaMemcpyAsync(dst, host, n * 8, cudaMemcpyHostToDevice, h->stream));
+    } else {
+        chfpe_status st = ensure_stage64(h);
+        if (st) return st;
+        CK(cudaMemcpyAsync(h->stage64, host, n * 8, cudaMemcpyHostToDevice, h->stream));
+        convert_kernel<double, float><<<1184, 256, 0, h->stream>>>(h->stage64, (float *)dst, n);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return CHFPE_OK;
+}
+
+static chfpe_status download(const chfpe_handle *hc, const void *src, double *host) {
+    chfpe_handle *h = const_cast<chfpe_handle *>(hc);
+    if (!host) return fail(CHFPE_EINVAL, "null host pointer");
+    const size_t n = (size_t)h->state;
+    if (h->prec == 64) {
+        CK(cudaMemcpyAsync(host, src, n * 8, cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        chfpe_status st = ensure_stage64(h);
+        if (st) return st;
+        convert_kernel<float, double><<<1184, 256, 0, h->stream>>>((const float *)src, h->stage64, n);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(host, h->stage64, n * 8, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_set_equilibrium(chfpe_handle *h, const double *host) {
+    if (!h) return fail(CHFPE_EINVAL, "null handle");
+    chfpe_status st = upload(h, host, h->eq);
+    if (!st) h->have_eq = true;
+    return st;
+}
+
+extern "C" chfpe_status chfpe_get_equilibrium(const chfpe_handle *h, double *host) {
+    if (!h) return fail(CHFPE_EINVAL, "null handle");
+    if (!h->have_eq) return fail(CHFPE_ESTATE, "no equilibrium yet");
+    return download(h, h->eq, host);
+}
+
+extern "C" chfpe_status chfpe_set_state(chfpe_handle *h, const double *host) {
+    if (!h) return fail(CHFPE_EINVAL, "null handle");
+    chfpe_status st = upload(h, host, h->cy);
+    if (!st) h->have_state = true;
+    return st;
+}
+
+extern "C" chfpe_status chfpe_get_state(const chfpe_handle *h, double *host) {
+    if (!h) return fail(CHFPE_EINVAL, "null handle");
+    if (!h->have_state) return fail(CHFPE_ESTATE, "no working state yet");
+    return download(h, h->cy, host);
+}
+
+extern "C" chfpe_status chfpe_propagate(chfpe_handle *h, long nsteps) {
+    if (!h) return fail(CHFPE_EINVAL, "null handle");
+    if (nsteps < 0) return fail(CHFPE_EINVAL, "nsteps < 0");
+    if (!h->have_state) return fail(CHFPE_ESTATE, "no working state yet");
+    chfpe_status st = rk4_any(h, h->cy, h->ca, h->cb, 1, nsteps);
+    if (st) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    return CHFPE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// equilibration (FP64)
+// ------------------------------------------------------------------------------------------
+
+static chfpe_status absmax(chfpe_handle *h, const double *x, double *result) {
+    const int nblk = 1024;
+    absmax_partial_kernel<double, 256><<<nblk, 256, 0, h->stream>>>(x, h->state, h->partial);
+    CK(cudaGetLastError());
+    std::vector<double> part(nblk);
+    CK(cudaMemcpyAsync(part.data(), h->partial, nblk * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double m = 0.0;
+    for (double v : part) m = (v > m || v != v) ? v : m;
+    *result = m;
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_equilibrate(chfpe_handle *h, long max_steps, double tol,
+                                          long check_every, long *steps_out, double *residual_out) {
+    if (!h) return fail(CHFPE_EINVAL, "null handle");
+    if (max_steps < 0 || check_every < 1) return fail(CHFPE_EINVAL, "max_steps >= 0, check_every >= 1");
+    chfpe_status st = CHFPE_OK;
+    const size_t n = (size_t)h->state;
+    double *y, *za, *zb;
+    double *tmp[3] = {nullptr, nullptr, nullptr};
+    if (h->prec == 64) {
+        y = (double *)h->cy; za = (double *)h->ca; zb = (double *)h->cb;
+    } else {
+        for (int i = 0; i < 3 && !st; ++i) tmp[i] = dalloc<double>(n, &st);
+        if (st) { for (double *p : tmp) if (p) cudaFree(p); return st; }
+        y = tmp[0]; za = tmp[1]; zb = tmp[2];
+    }
+    auto cleanup = [&]() { for (double *p : tmp) if (p) cudaFree(p); };
+
+    // g^(0) = exp(-H/2kT) / Z, other members zero
+    CK(cudaMemsetAsync(y, 0, n * 8, h->stream));
+    const int nblk = 296;
+    boltzmann_kernel<256><<<nblk, 256, 0, h->stream>>>(y, h->P, h->Pp, h->d, h->U_d, h->np_d,
+                                                        h->plo_d, h->ph_d, h->inv2m_d,
+                                                        0.5 / h->model.kT, h->partial, nblk);
+    double vol = 1.0;
+    for (int ax = 0; ax < 2 * h->d; ++ax) vol *= h->h[ax];
+    scale_by_sum_kernel<<<296, 256, 0, h->stream>>>(y, h->P, h->partial, nblk, vol);
+    cudaError_t e = cudaGetLastError();
+    if (e) { cleanup(); return fail(CHFPE_ECUDA, cudaGetErrorString(e)); }
+
+    auto residual = [&](double *r) -> chfpe_status {
+        chfpe_status s2 = stage<double>(h, y, nullptr, za, 1.0, 1);
+        if (s2) return s2;
+        double km, wm;
+        if ((s2 = absmax(h, za, &km))) return s2;
+        if ((s2 = absmax(h, y, &wm))) return s2;
+        *r = km / wm;
+        return CHFPE_OK;
+    };
+    // the stage kernel is dispatched on the handle's precision only through its template
+    // argument, so FP64 equilibration works for either handle precision
+    long steps = 0;
+    double r = 0.0;
+    if ((st = residual(&r))) { cleanup(); return st; }
+    while (steps < max_steps && r >= tol) {
+        long k = std::min(check_every, max_steps - steps);
+        if ((st = rk4<double>(h, y, za, zb, 1, k))) { cleanup(); return st; }
+        steps += k;
+        if ((st = residual(&r))) { cleanup(); return st; }
+        if (!std::isfinite(r)) { cleanup(); return fail(CHFPE_EUNSTABLE, "equilibration diverged"); }
+    }
+    if (h->prec == 64) {
+        e = cudaMemcpyAsync(h->eq, y, n * 8, cudaMemcpyDeviceToDevice, h->stream);
+    } else {
+        convert_kernel<double, float><<<1184, 256, 0, h->stream>>>(y, (float *)h->eq, n);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaStreamSynchronize(h->stream);
+    cleanup();
+    if (e) return fail(CHFPE_ECUDA, cudaGetErrorString(e));
+    h->have_eq = true;
+    if (steps_out) *steps_out = steps;
+    if (residual_out) *residual_out = r;
+    return CHFPE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// response functions
+// ------------------------------------------------------------------------------------------
+
+static chfpe_status ensure_dR(chfpe_handle *h, size_t n) {
+    if (h->dR_cap >= n) return CHFPE_OK;
+    if (h->dR) cudaFree(h->dR);
+    h->dR = nullptr;
+    chfpe_status st = CHFPE_OK;
+    h->dR = dalloc<double>(n, &st);
+    h->dR_cap = st ? 0 : n;
+    return st;
+}
+
+static chfpe_status finish_response(chfpe_handle *h, double *R, size_t n) {
+    CK(cudaMemcpyAsync(R, h->dR, n * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(R[i])) return fail(CHFPE_EUNSTABLE, "non-finite response value");
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_response1(chfpe_handle *h, const chfpe_optical *A,
+                                        const chfpe_optical *C, int nt, int stride, double *R) {
+    if (!h || !A || !C || !R) return fail(CHFPE_EINVAL, "null argument");
+    if (nt < 1 || stride < 0) return fail(CHFPE_EINVAL, "nt >= 1, stride >= 0");
+    if (!h->have_eq) return fail(CHFPE_ESTATE, "no equilibrium: call chfpe_equilibrate or chfpe_set_equilibrium");
+    chfpe_status st;
+    if ((st = ensure_dR(h, nt))) return st;
+    if ((st = set_observable(h, C))) return st;
+    if ((st = insert(h, A, h->eq, 0, h->cy, 1))) return st;
+    for (int k = 0; k < nt; ++k) {
+        if ((st = observe(h, h->cy, 1, h->dR + k, 1))) return st;
+        if (k + 1 < nt && (st = rk4_any(h, h->cy, h->ca, h->cb, 1, stride))) return st;
+    }
+    h->have_state = true;
+    return finish_response(h, R, nt);
+}
+
+extern "C" chfpe_status chfpe_response2(chfpe_handle *h, const chfpe_optical *A,
+                                        const chfpe_optical *B, const chfpe_optical *C, int nt1,
+                                        int nt2, int stride, double *R) {
+    if (!h || !A || !B || !C || !R) return fail(CHFPE_EINVAL, "null argument");
+    if (nt1 < 1 || nt2 < 1 || stride < 0) return fail(CHFPE_EINVAL, "nt1, nt2 >= 1, stride >= 0");
+    if (!h->have_eq) return fail(CHFPE_ESTATE, "no equilibrium: call chfpe_equilibrate or chfpe_set_equilibrium");
+    chfpe_status st;
+    const size_t total = (size_t)nt1 * nt2;
+    if ((st = ensure_dR(h, total))) return st;
+    if ((st = set_observable(h, C))) return st;
+    // t1 chain
+    if ((st = insert(h, A, h->eq, 0, h->cy, 1))) return st;
+    const int cap = h->opts.max_batch;
+    const size_t sbytes = (size_t)h->state * h->esize;
+    for (int i0 = 0; i0 < nt1; i0 += cap) {
+        const int nb = std::min(cap, nt1 - i0);
+        // spawn the branches of this chunk along the chain
+        for (int c = 0; c < nb; ++c) {
+            if ((st = insert(h, B, h->cy, 0, (char *)h->by + c * sbytes, 1))) return st;
+            if (i0 + c + 1 < nt1 && (st = rk4_any(h, h->cy, h->ca, h->cb, 1, stride))) return st;
+        }
+        // advance the chunk's branches in lockstep
+        for (int j = 0; j < nt2; ++j) {
+            if ((st = observe(h, h->by, nb, h->dR + (size_t)i0 * nt2 + j, nt2))) return st;
+            if (j + 1 < nt2 && (st = rk4_any(h, h->by, h->ba, h->bb, nb, stride))) return st;
+        }
+    }
+    h->have_state = true;
+    return finish_response(h, R, total);
+}
+
+// ------------------------------------------------------------------------------------------
+// device-buffer entry points
+// ------------------------------------------------------------------------------------------
+
+extern "C" chfpe_status chfpe_rhs_device(chfpe_handle *h, const void *in, void *out, int batch) {
+    if (!h || !in || !out || batch < 1 || batch > 65535) return fail(CHFPE_EINVAL, "bad argument");
+    chfpe_status st = h->prec == 64 ? stage<double>(h, in, nullptr, out, 1.0, batch)
+                                    : stage<float>(h, in, nullptr, out, 1.0, batch);
+    if (st) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_rk4_device(chfpe_handle *h, void *states, int batch, long nsteps) {
+    if (!h || !states || batch < 1 || nsteps < 0) return fail(CHFPE_EINVAL, "bad argument");
+    if (batch > h->opts.max_batch) return fail(CHFPE_EINVAL, "batch > max_batch");
+    chfpe_status st = rk4_any(h, states, h->ba, h->bb, batch, nsteps);
+    if (st) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_insert_device(chfpe_handle *h, const chfpe_optical *X, const void *in,
+                                            void *out, int batch) {
+    if (!h || !X || !in || !out || batch < 1 || batch > 65535) return fail(CHFPE_EINVAL, "bad argument");
+    chfpe_status st = insert(h, X, in, h->state, out, batch);
+    if (st) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_observe_device(chfpe_handle *h, const chfpe_optical *C, const void *in,
+                                             int batch, double *R_dev) {
+    if (!h || !C || !in || !R_dev || batch < 1 || batch > 65535) return fail(CHFPE_EINVAL, "bad argument");
+    chfpe_status st;
+    if ((st = set_observable(h, C))) return st;
+    if ((st = observe(h, in, batch, R_dev, 1))) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    return CHFPE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// save / load the equilibrium
+// ------------------------------------------------------------------------------------------
+
+struct EqHeader {
+    char magic[8];
+    int d, depth, M, pad;
+    int nq[3], np[3];
+    double qmin[3], qmax[3], pmin[3], pmax[3];
+    long long P;
+};
+
+static EqHeader make_header(const chfpe_handle *h) {
+    EqHeader hd;
+    memset(&hd, 0, sizeof hd);
+    memcpy(hd.magic, "CHFPEQ1", 8);
+    hd.d = h->d;
+    hd.depth = h->depth;
+    hd.M = h->M;
+    for (int s = 0; s < 3; ++s) {
+        hd.nq[s] = s < h->d ? h->grid.nq[s] : 0;
+        hd.np[s] = s < h->d ? h->grid.np[s] : 0;
+        hd.qmin[s] = s < h->d ? h->grid.qmin[s] : 0;
+        hd.qmax[s] = s < h->d ? h->grid.qmax[s] : 0;
+        hd.pmin[s] = s < h->d ? h->grid.pmin[s] : 0;
+        hd.pmax[s] = s < h->d ? h->grid.pmax[s] : 0;
+    }
+    hd.P = h->P;
+    return hd;
+}
+
+extern "C" chfpe_status chfpe_save_equilibrium(const chfpe_handle *h, const char *path) {
+    if (!h || !path) return fail(CHFPE_EINVAL, "null argument");
+    if (!h->have_eq) return fail(CHFPE_ESTATE, "no equilibrium yet");
+    std::vector<double> buf((size_t)h->state);
+    chfpe_status st = download(h, h->eq, buf.data());
+    if (st) return st;
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(CHFPE_EINVAL, std::string("cannot open ") + path);
+    EqHeader hd = make_header(h);
+    bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 &&
+              fwrite(buf.data(), 8, buf.size(), f) == buf.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? CHFPE_OK : fail(CHFPE_EINVAL, std::string("write failed: ") + path);
+}
+
+extern "C" chfpe_status chfpe_load_equilibrium(chfpe_handle *h, const char *path) {
+    if (!h || !path) return fail(CHFPE_EINVAL, "null argument");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(CHFPE_EINVAL, std::string("cannot open ") + path);
+    EqHeader hd, want = make_header(h);
+    std::vector<double> buf((size_t)h->state);
+    bool ok = fread(&hd, sizeof hd, 1, f) == 1;
+    if (ok && memcmp(&hd, &want, sizeof hd) != 0) {
+        fclose(f);
+        return fail(CHFPE_EINVAL, "equilibrium file does not match this grid / depth");
+    }
+    ok = ok && fread(buf.data(), 8, buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) return fail(CHFPE_EINVAL, std::string("short read: ") + path);
+    return chfpe_set_equilibrium(h, buf.data());
+}
+
+// ------------------------------------------------------------------------------------------
+// measurement counters
+// ------------------------------------------------------------------------------------------
+
+extern "C" chfpe_status chfpe_stats_reset(chfpe_handle *h, int time_stages) {
+    if (!h) return fail(CHFPE_EINVAL, "null handle");
+    CK(cudaStreamSynchronize(h->stream));
+    h->launches = h->stage_launches = 0;
+    h->stage_bytes = h->cell_updates = 0.0;
+    h->time_stages = time_stages != 0;
+    h->ev_used = 0;
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_stats_get(chfpe_handle *h, chfpe_stats *out) {
+    if (!h || !out) return fail(CHFPE_EINVAL, "null argument");
+    CK(cudaStreamSynchronize(h->stream));
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]));
+        ms += t;
+    }
+    out->kernel_launches = h->launches;
+    out->stage_launches = h->stage_launches;
+    out->stage_ms = ms;
+    out->stage_bytes = h->stage_bytes;
+    out->cell_updates = h->cell_updates;
+    return CHFPE_OK;
+}

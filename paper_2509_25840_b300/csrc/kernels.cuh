@@ -1,0 +1,399 @@
+// kernels.cuh -- CUDA kernels of the CHFPE hot path for sm_103a.
+//
+// All kernels work on the symmetrised members g^(n) = W^(n) exp(H/2kT) / lambda_n (Appendix A's
+// exp(-H/2kT) prefactor) stored [batch][member][q_1..q_d][p_1..p_d], p_d fastest.
+//
+//   stage_kernel    out = y + c * (M in)   (or out = M in when y == nullptr), where M is the
+//                   right-hand side of Eq. HEOM in symmetrised form:
+//                     (M g)^(n) = sum_s [dU/dq_s D_ps g^(n) - (p_s/m_s) D_qs g^(n)]
+//                               - sum_s n_s gamma_s g^(n)
+//                               + sum_s sqrt((n_s+1)c_s) V_s' (D_ps - p_s/2m_skT) g^(n+e_s)
+//                               + sum_s sqrt(n_s c_s)     V_s' (D_ps + p_s/2m_skT) g^(n-e_s)
+//                   (Eqs. CL_liouville, Phi, Theta; c_s = zeta_s gamma_s m_s kT).  One thread
+//                   owns one grid point for every member: each member's p-derivatives are formed
+//                   once and pushed to the member itself and to its two neighbours per mode.
+//   insert_kernel   out^(n) = sum_s dX/dq_s (D_ps - p_s/2m_skT) g^(n)      (Eq. Opticalexc)
+//   observe_*       R = h^2d sum C(q) exp(-H/2kT) g^(0), FP64 accumulation, two passes
+//                   (per-block partials, then a fixed-order sum: deterministic)
+//   boltzmann_*     g^(0) = exp(-H/2kT) / Z, Z = h^2d sum exp(-H/kT)        (Sec. IV B start)
+//   absmax_*        max |x| over a state (equilibration residual)
+//
+// D_x f = (45 (f+1 - f-1) - 9 (f+2 - f-2) + (f+3 - f-3)) / (60 h), zero outside the grid; the
+// 1/(60 h) factors are folded into the coefficients.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace chfpe {
+
+constexpr int kMaxD = 3;
+constexpr int kMaxDepth = 8;
+
+// ------------------------------------------------------------------------------------------
+// compile-time hierarchy member tables: by tier, then lexicographically ascending
+// ------------------------------------------------------------------------------------------
+
+constexpr int member_count(int d, int depth) {
+    int M = 0;
+    for (int t = 0; t <= depth; ++t) {
+        long c = 1;
+        for (int k = 1; k < d; ++k) c = c * (t + k) / k;
+        M += (int)c;
+    }
+    return M;
+}
+
+template <int D, int DEPTH>
+struct MemberTable {
+    static constexpr int M = member_count(D, DEPTH);
+    int n[M][3];
+    int up[M][3];   // index of n + e_s, or -1
+    int dn[M][3];   // index of n - e_s, or -1
+    constexpr MemberTable() : n{}, up{}, dn{} {
+        int c = 0;
+        for (int t = 0; t <= DEPTH; ++t) {
+            if (D == 1) {
+                n[c][0] = t; n[c][1] = 0; n[c][2] = 0; ++c;
+            } else if (D == 2) {
+                for (int a = 0; a <= t; ++a) { n[c][0] = a; n[c][1] = t - a; n[c][2] = 0; ++c; }
+            } else {
+                for (int a = 0; a <= t; ++a)
+                    for (int b = 0; b <= t - a; ++b) {
+                        n[c][0] = a; n[c][1] = b; n[c][2] = t - a - b; ++c;
+                    }
+            }
+        }
+        for (int i = 0; i < M; ++i)
+            for (int s = 0; s < 3; ++s) {
+                up[i][s] = -1;
+                dn[i][s] = -1;
+                if (s >= D) continue;
+                for (int j = 0; j < M; ++j) {
+                    bool isup = true, isdn = true;
+                    for (int r = 0; r < 3; ++r) {
+                        int want_up = n[i][r] + (r == s ? 1 : 0);
+                        int want_dn = n[i][r] - (r == s ? 1 : 0);
+                        if (n[j][r] != want_up) isup = false;
+                        if (n[j][r] != want_dn) isdn = false;
+                    }
+                    if (isup) up[i][s] = j;
+                    if (isdn) dn[i][s] = j;
+                }
+            }
+    }
+};
+
+// ------------------------------------------------------------------------------------------
+// kernel arguments (passed by value)
+// ------------------------------------------------------------------------------------------
+
+template <typename T>
+struct StageArgs {
+    const T *in;          // stencil input, batch of states
+    const T *y;           // base state (same batch layout) or nullptr: out = c * M in
+    T *out;
+    long long state;      // values per state (M * P)
+    int P;                // points per member
+    int n[6];             // axis sizes: q_1..q_d, p_1..p_d
+    int st[6];            // axis strides inside one member
+    int Pp;               // points of the p-subgrid (q index = x / Pp)
+    int NQ;               // points of the q-subgrid
+    T c;                  // stage coefficient
+    const T *F;           // [D][NQ]  dU/dq_s / (60 h_ps)
+    T qlo[3], qh[3], plo[3], ph[3];
+    T vq[3];              // 1 / (m_s 60 h_qs)
+    T inv60hp[3];         // 1 / (60 h_ps)
+    T kappa[3];           // 1 / (2 m_s kT)
+    T VLL[3], VSL[3];
+    T gam[3];
+    T link[3][kMaxDepth + 2];   // sqrt(k c_s)
+};
+
+template <typename T>
+__device__ __forceinline__ T stencil7(const T *__restrict__ f, int x, int i, int N, int st) {
+    // (45 (f+1 - f-1) - 9 (f+2 - f-2) + (f+3 - f-3)), zero outside [0, N)
+    T p1 = (i + 1 < N) ? __ldg(f + x + st) : T(0);
+    T m1 = (i >= 1) ? __ldg(f + x - st) : T(0);
+    T p2 = (i + 2 < N) ? __ldg(f + x + 2 * st) : T(0);
+    T m2 = (i >= 2) ? __ldg(f + x - 2 * st) : T(0);
+    T p3 = (i + 3 < N) ? __ldg(f + x + 3 * st) : T(0);
+    T m3 = (i >= 3) ? __ldg(f + x - 3 * st) : T(0);
+    return T(45) * (p1 - m1) - T(9) * (p2 - m2) + (p3 - m3);
+}
+
+// ------------------------------------------------------------------------------------------
+// fused RHS + RK4 stage
+// ------------------------------------------------------------------------------------------
+
+template <typename T, int D, int DEPTH>
+__global__ void __launch_bounds__(256) stage_kernel(const StageArgs<T> a) {
+    constexpr MemberTable<D, DEPTH> tab{};
+    constexpr int M = MemberTable<D, DEPTH>::M;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= a.P) return;
+    const long long boff = (long long)blockIdx.y * a.state;
+    const T *__restrict__ in = a.in + boff;
+
+    int idx[2 * D];
+    {
+        int r = x;
+#pragma unroll
+        for (int ax = 2 * D - 1; ax >= 0; --ax) {
+            idx[ax] = r % a.n[ax];
+            r /= a.n[ax];
+        }
+    }
+    const int qlin = x / a.Pp;
+
+    T Fs[D], vq[D], VpD[D], VpK[D];
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+        const T q = a.qlo[s] + T(idx[s]) * a.qh[s];
+        const T p = a.plo[s] + T(idx[D + s]) * a.ph[s];
+        const T Vp = a.VLL[s] + a.VSL[s] * q;
+        Fs[s] = __ldg(a.F + s * a.NQ + qlin);
+        vq[s] = p * a.vq[s];
+        VpD[s] = Vp * a.inv60hp[s];
+        VpK[s] = Vp * a.kappa[s] * p;
+    }
+
+    T acc[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] = T(0);
+
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const T *__restrict__ g = in + (long long)m * a.P;
+        const T v = __ldg(g + x);
+        T dp[D];
+        T k = T(0);
+        T gm = T(0);
+#pragma unroll
+        for (int s = 0; s < D; ++s) {
+            const T dq = stencil7(g, x, idx[s], a.n[s], a.st[s]);
+            dp[s] = stencil7(g, x, idx[D + s], a.n[D + s], a.st[D + s]);
+            k += Fs[s] * dp[s] - vq[s] * dq;
+            gm += T(tab.n[m][s]) * a.gam[s];
+        }
+        acc[m] += k - gm * v;
+#pragma unroll
+        for (int s = 0; s < D; ++s) {
+            if (tab.dn[m][s] >= 0) {
+                const T w = a.link[s][tab.n[m][s]];
+                acc[tab.dn[m][s]] += w * (VpD[s] * dp[s] - VpK[s] * v);
+            }
+            if (tab.up[m][s] >= 0) {
+                const T w = a.link[s][tab.n[m][s] + 1];
+                acc[tab.up[m][s]] += w * (VpD[s] * dp[s] + VpK[s] * v);
+            }
+        }
+    }
+
+    T *__restrict__ out = a.out + boff;
+    if (a.y) {
+        const T *__restrict__ y = a.y + boff;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const long long o = (long long)m * a.P + x;
+            out[o] = y[o] + a.c * acc[m];
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) out[(long long)m * a.P + x] = a.c * acc[m];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// optical insertion X^x, every member (Eq. Opticalexc, symmetrised)
+// ------------------------------------------------------------------------------------------
+
+template <typename T>
+struct InsertArgs {
+    const T *in;
+    T *out;
+    long long in_state, out_state;   // batch strides (in_state may be 0: one input, many outputs)
+    int P, M, d;
+    int n[6], st[6];
+    T qlo[3], qh[3], plo[3], ph[3];
+    T lin[3];
+    T quad[3][3];                    // symmetric part of the quadratic coefficients
+    T inv60hp[3], kappa[3];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) insert_kernel(const InsertArgs<T> a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= a.P) return;
+    const T *__restrict__ in = a.in + (long long)blockIdx.y * a.in_state;
+    T *__restrict__ out = a.out + (long long)blockIdx.y * a.out_state;
+    const int d = a.d;
+    int idx[6];
+    int r = x;
+    for (int ax = 2 * d - 1; ax >= 0; --ax) {
+        idx[ax] = r % a.n[ax];
+        r /= a.n[ax];
+    }
+    T G[3], Kp[3];
+    for (int s = 0; s < d; ++s) {
+        T gs = a.lin[s];
+        for (int b = 0; b < d; ++b) gs += a.quad[s][b] * (a.qlo[b] + T(idx[b]) * a.qh[b]);
+        const T p = a.plo[s] + T(idx[d + s]) * a.ph[s];
+        G[s] = gs * a.inv60hp[s];
+        Kp[s] = gs * a.kappa[s] * p;
+    }
+    for (int m = 0; m < a.M; ++m) {
+        const T *__restrict__ g = in + (long long)m * a.P;
+        const T v = __ldg(g + x);
+        T acc = T(0);
+        for (int s = 0; s < d; ++s) {
+            const T dp = stencil7(g, x, idx[d + s], a.n[d + s], a.st[d + s]);
+            acc += G[s] * dp - Kp[s] * v;
+        }
+        out[(long long)m * a.P + x] = acc;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// reductions (FP64)
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_down_sync(0xffffffffu, v, o);
+        v = (u > v || u != u) ? u : v;      // NaN propagates
+    }
+    return v;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[NT / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < NT / 32) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    return v;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max(double v) {
+    __shared__ double sh[NT / 32];
+    v = warp_max(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < NT / 32) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_max(v);
+    return v;
+}
+
+struct ObserveArgs {
+    const void *in;          // batch of states (T), member 0 is read
+    long long state;
+    int P, Pp, d;
+    int np[3];               // p-axis sizes
+    const double *CWq;       // [NQ]: C(q) exp(-U(q)/2kT)
+    const double *wp;        // [3][maxnp]: exp(-p^2 / 4 m_s kT)
+    int wp_ld;
+    double *partial;         // [batch][nblk]
+    int nblk;
+};
+
+// block b of state j sums points b, b + nblk*NT, ... (grid-stride) into partial[j][b]
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) observe_partial_kernel(const ObserveArgs a) {
+    const T *__restrict__ g = (const T *)a.in + (long long)blockIdx.y * a.state;
+    double sum = 0.0;
+    for (int x = blockIdx.x * NT + threadIdx.x; x < a.P; x += a.nblk * NT) {
+        const int qlin = x / a.Pp;
+        int r = x - qlin * a.Pp;
+        double w = a.CWq[qlin];
+        for (int s = a.d - 1; s >= 0; --s) {
+            const int ip = r % a.np[s];
+            r /= a.np[s];
+            w *= a.wp[s * a.wp_ld + ip];
+        }
+        sum += w * (double)g[x];
+    }
+    sum = block_sum<NT>(sum);
+    if (threadIdx.x == 0) a.partial[(long long)blockIdx.y * a.nblk + blockIdx.x] = sum;
+}
+
+// out[j * out_stride] = scale * sum_b partial[j][b], fixed order; one warp per state
+__global__ void observe_finish_kernel(const double *partial, int nblk, int batch, double scale,
+                                      double *out, long long out_stride) {
+    const int j = blockIdx.x;
+    if (j >= batch) return;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += partial[(long long)j * nblk + b];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) out[(long long)j * out_stride] = scale * s;
+}
+
+// Boltzmann: g0[x] = exp(-(U(q) + sum p^2/2m) / 2kT); partial sums of g0^2
+template <int NT>
+__global__ void __launch_bounds__(NT) boltzmann_kernel(double *g0, int P, int Pp, int d,
+                                                       const double *Uq, const int *np,
+                                                       const double *plo, const double *ph,
+                                                       const double *inv2m, double inv2kT,
+                                                       double *partial, int nblk) {
+    double sum = 0.0;
+    for (int x = blockIdx.x * NT + threadIdx.x; x < P; x += nblk * NT) {
+        const int qlin = x / Pp;
+        int r = x - qlin * Pp;
+        double E = Uq[qlin];
+        for (int s = d - 1; s >= 0; --s) {
+            const int ip = r % np[s];
+            r /= np[s];
+            const double p = plo[s] + ip * ph[s];
+            E += p * p * inv2m[s];
+        }
+        const double v = exp(-E * inv2kT);
+        g0[x] = v;
+        sum += v * v;
+    }
+    sum = block_sum<NT>(sum);
+    if (threadIdx.x == 0) partial[blockIdx.x] = sum;
+}
+
+__global__ void scale_by_sum_kernel(double *g, long long n, const double *partial, int nblk,
+                                    double vol) {
+    // g *= 1 / (vol * sum partial), the sum taken in fixed order by every thread
+    double Z = 0.0;
+    for (int b = 0; b < nblk; ++b) Z += partial[b];
+    const double s = 1.0 / (vol * Z);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        g[i] *= s;
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) absmax_partial_kernel(const T *x, long long n,
+                                                            double *partial) {
+    double m = 0.0;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n;
+         i += (long long)gridDim.x * NT) {
+        const double v = fabs((double)x[i]);
+        m = (v > m || v != v) ? v : m;      // NaN propagates
+    }
+    m = block_max<NT>(m);
+    if (threadIdx.x == 0) partial[blockIdx.x] = m;
+}
+
+template <typename S, typename D_>
+__global__ void convert_kernel(const S *in, D_ *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (D_)in[i];
+}
+
+}  // namespace chfpe

@@ -1,0 +1,55 @@
+"""CPU checks of the C-ABI library: it loads, exports every function include/chfpe.h declares,
+and rejects invalid arguments before touching a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2509_25840_b300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(chfpe_\w+)\s*\(", text))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = libbuild.build()
+    declared = _declared()
+    assert {"chfpe_create", "chfpe_response2", "chfpe_equilibrate"} <= declared
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (chfpe_\w+)", out))
+    missing = declared - exported
+    assert not missing, missing
+    ctypes.CDLL(lib)       # loads without a GPU
+
+
+def test_create_rejects_invalid_arguments_on_cpu():
+    from paper_2509_25840_b300 import chfpe, inputs
+    libbuild.build()
+    wl = inputs.one_mode_64()
+    bad = [
+        dict(depth=9),                 # beyond the compiled range for one mode
+        dict(dt=1.0),                  # above the RK4 stability bound
+        dict(precision=16),
+        dict(max_batch=0),
+    ]
+    for kw in bad:
+        args = dict(depth=wl.depth, dt=wl.dt, precision=32, max_batch=1)
+        args.update(kw)
+        with pytest.raises(chfpe.ChfpeError) as e:
+            chfpe.Handle(wl.model, wl.grid, **args)
+        assert e.value.status == chfpe.EINVAL, (kw, str(e.value))
+    small = inputs.Grid(nq=(6,), np=(64,), qmin=(-6,), qmax=(6,), pmin=(-6,), pmax=(6,))
+    with pytest.raises(chfpe.ChfpeError):
+        chfpe.Handle(wl.model, small, depth=2, dt=0.005)

@@ -1,0 +1,214 @@
+"""GPU parity: libchfpe (through its C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: FP64 path 1e-10 (normalised L-infinity on responses, relative to max |oracle| on
+operator outputs); FP32 path 1e-4 on normalised responses.  Operator-level FP32 checks compare
+against the oracle evaluated on the float-rounded input, so only arithmetic rounding differs; the
+bound there is a few float ulps times the size of the largest single term."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_25840_b300 import inputs
+import references as ref
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_25840_b300 import build
+    build.build()
+
+
+def _chfpe():
+    from paper_2509_25840_b300 import chfpe
+    return chfpe
+
+
+def _dtype(prec):
+    return torch.float64 if prec == 64 else torch.float32
+
+
+def _rounded(W, prec):
+    return W if prec == 64 else W.astype(np.float32).astype(np.float64)
+
+
+def _model(d):
+    return inputs.Model(nmodes=d, kT=0.9, m=(1.2, 0.8, 1.0), omega=(1.0, 1.3, 0.7),
+                        g3=(0.2, -0.15, 0.1), g4=(0.05, 0.04, 0.06),
+                        g2=[[0, 0.1, 0.05], [0, 0, -0.1]], g_s2s=[[0, 0.2, 0.1], [0, 0, 0.1]],
+                        g_ss2=[[0, 0.12, 0.1], [0, 0, 0.05]], zeta=(0.5, 0.3, 0.4),
+                        gamma=(1.0, 1.5, 0.8), V_LL=(1.0, 0.7, 0.9), V_SL=(0.3, -0.4, 0.2))
+
+
+# ragged per-axis sizes: several 256-thread tiles plus a tail in every case
+CASES = [
+    (1, [37, 45], 5),
+    (1, [64, 64], 8),
+    (2, [9, 11, 13, 15], 4),
+    (2, [12, 10, 14, 9], 5),
+    (3, [7, 8, 9, 7, 8, 9], 2),
+    (3, [7, 7, 8, 8, 7, 9], 3),
+]
+
+
+def _setup(d, n, depth, prec, max_batch=1, dt=0.004):
+    chfpe = _chfpe()
+    model = _model(d)
+    grid = inputs.default_grid(model, n, cut=12.0, nsigma=5.0)
+    h = chfpe.Handle(model, grid, depth=depth, dt=dt, precision=prec, max_batch=max_batch)
+    pb = oracle.Problem(model, grid, depth)
+    return model, grid, h, pb
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("d,n,depth", CASES)
+def test_rhs_matches_oracle(d, n, depth, prec):
+    model, grid, h, pb = _setup(d, n, depth, prec)
+    W = _rounded(inputs.random_state(grid, pb.M, seed=100 + d, smooth=False), prec)
+    want = oracle.rhs(pb, W)
+    x = torch.tensor(W, dtype=_dtype(prec), device="cuda")
+    y = torch.empty_like(x)
+    h.rhs_device(x.data_ptr(), y.data_ptr(), 1)
+    got = y.double().cpu().numpy()
+    scale = np.abs(want).max()
+    tol = 1e-13 if prec == 64 else 3e-6
+    assert np.abs(got - want).max() <= tol * scale
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("d,n,depth", CASES[::2])
+def test_insert_and_observe_match_oracle(d, n, depth, prec):
+    model, grid, h, pb = _setup(d, n, depth, prec)
+    W = _rounded(inputs.random_state(grid, pb.M, seed=7, smooth=True), prec)
+    X = inputs.Optical(lin=(0.7, -1.1, 0.4), quad=[[0.4, 0.9, 0.1], [0.1, -0.6, 0.2], [0.3, 0.0, 0.5]])
+    want = oracle.insert(pb, X, W)
+    x = torch.tensor(W, dtype=_dtype(prec), device="cuda")
+    y = torch.empty_like(x)
+    h.insert_device(X, x.data_ptr(), y.data_ptr(), 1)
+    got = y.double().cpu().numpy()
+    tol = 1e-13 if prec == 64 else 3e-6
+    assert np.abs(got - want).max() <= tol * np.abs(want).max()
+    # observable: FP64 accumulation on both sides of the same (rounded) values
+    Rd = torch.zeros(2, dtype=torch.float64, device="cuda")
+    xx = torch.stack([x, 2.0 * x])
+    h.observe_device(X, xx.data_ptr(), 2, Rd.data_ptr())
+    r = Rd.cpu().numpy()
+    r0 = oracle.observe(pb, X, W)
+    assert r[0] == pytest.approx(r0, rel=1e-12, abs=1e-14)
+    assert r[1] == pytest.approx(2 * r0, rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("d,n,depth", [CASES[0], CASES[2], CASES[4]])
+def test_rk4_matches_oracle_and_batches_are_independent(d, n, depth, prec):
+    model, grid, h, pb = _setup(d, n, depth, prec, max_batch=3)
+    W = _rounded(inputs.random_state(grid, pb.M, seed=5, smooth=True), prec)
+    nsteps = 25
+    want = oracle.rk4(pb, W, 0.004, nsteps)
+    x = torch.tensor(np.stack([W, 0.5 * W, W]), dtype=_dtype(prec), device="cuda")
+    h.rk4_device(x.data_ptr(), 3, nsteps)
+    got = x.double().cpu().numpy()
+    tol = 1e-12 if prec == 64 else 2e-5
+    scale = np.abs(want).max()
+    assert np.abs(got[0] - want).max() <= tol * scale
+    assert np.abs(got[1] - 0.5 * want).max() <= tol * scale
+    assert np.array_equal(got[0], got[2])           # batch slots do not interact
+
+
+def _norm_err(got, want):
+    return np.abs(got - want).max() / np.abs(want).max()
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-10), (32, 1e-4)])
+def test_response1_one_mode_matches_oracle(prec, tol):
+    wl = inputs.one_mode_64(nt=201, stride=2)
+    chfpe = _chfpe()
+    pb = oracle.Problem(wl.model, wl.grid, wl.depth)
+    Weq, _, _ = oracle.equilibrate(pb, wl.dt, 200, 0.0, 100)
+    want = oracle.response1(pb, wl.A, wl.C, _rounded(Weq, prec), wl.dt, wl.nt1, wl.stride)
+    with chfpe.Handle(wl.model, wl.grid, depth=wl.depth, dt=wl.dt, precision=prec) as h:
+        h.set_equilibrium(Weq)
+        got = h.response1(wl.A, wl.C, wl.nt1, wl.stride)
+    assert _norm_err(got, want) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-10), (32, 1e-4)])
+@pytest.mark.parametrize("d,n,depth", [(2, [14, 12, 16, 13], 3), (3, [8, 7, 9, 8, 7, 9], 2)])
+def test_response2_matches_oracle(d, n, depth, prec, tol):
+    chfpe = _chfpe()
+    model = _model(d)
+    grid = inputs.default_grid(model, n, cut=12.0, nsigma=5.0)
+    pb = oracle.Problem(model, grid, depth)
+    Weq = ref.hierarchy_state(ref.boltzmann_sym(model, grid), pb.M)
+    mu, Pi = inputs.three_mode_optics()
+    dt, nt1, nt2, stride = 0.004, 5, 4, 6
+    want = oracle.response2(pb, mu, Pi, mu, _rounded(Weq, prec), dt, nt1, nt2, stride)
+    with chfpe.Handle(model, grid, depth=depth, dt=dt, precision=prec, max_batch=3) as h:
+        h.set_equilibrium(Weq)
+        got = h.response2(mu, Pi, mu, nt1, nt2, stride)
+    assert _norm_err(got, want) < tol
+
+
+def test_response2_chunking_is_bitwise_invariant():
+    chfpe = _chfpe()
+    model = _model(2)
+    grid = inputs.default_grid(model, [11, 12, 13, 10], cut=12.0, nsigma=5.0)
+    pb = oracle.Problem(model, grid, 2)
+    Weq = ref.hierarchy_state(ref.boltzmann_sym(model, grid), pb.M)
+    mu, Pi = inputs.three_mode_optics()
+    out = []
+    for mb in (1, 3, 7):
+        with chfpe.Handle(model, grid, depth=2, dt=0.004, precision=64, max_batch=mb) as h:
+            h.set_equilibrium(Weq)
+            out.append(h.response2(Pi, mu, mu, 7, 5, 4))
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+def test_equilibrate_matches_oracle():
+    chfpe = _chfpe()
+    model = _model(2)
+    grid = inputs.default_grid(model, [12, 11, 13, 12], cut=12.0, nsigma=5.0)
+    pb = oracle.Problem(model, grid, 2)
+    want, steps_o, res_o = oracle.equilibrate(pb, 0.004, 300, 0.0, 100)
+    for prec in (64, 32):
+        with chfpe.Handle(model, grid, depth=2, dt=0.004, precision=prec) as h:
+            steps, res = h.equilibrate(300, 0.0, 100)
+            got = h.get_equilibrium()
+        assert steps == steps_o == 300
+        assert res == pytest.approx(res_o, rel=1e-9)
+        tol = 1e-12 if prec == 64 else 1e-7      # FP32 only rounds the FP64 result once
+        assert np.abs(got - want).max() <= tol * np.abs(want).max()
+
+
+def test_state_roundtrip_save_load_and_errors(tmp_path):
+    chfpe = _chfpe()
+    wl = inputs.one_mode_64(nt=3)
+    with chfpe.Handle(wl.model, wl.grid, depth=wl.depth, dt=wl.dt, precision=64) as h:
+        with pytest.raises(chfpe.ChfpeError) as e:
+            h.response1(wl.A, wl.C, 3, 1)
+        assert e.value.status == chfpe.ESTATE
+        W = inputs.random_state(wl.grid, h.members, seed=3)
+        h.set_equilibrium(W)
+        assert np.array_equal(h.get_equilibrium(), W)
+        p = str(tmp_path / "eq.bin")
+        h.save_equilibrium(p)
+        h.set_equilibrium(2 * W)
+        h.load_equilibrium(p)
+        assert np.array_equal(h.get_equilibrium(), W)
+        h.set_state(W)
+        h.propagate(3)
+        pb = oracle.Problem(wl.model, wl.grid, wl.depth)
+        np.testing.assert_allclose(h.get_state(), oracle.rk4(pb, W, wl.dt, 3), rtol=0,
+                                   atol=1e-12 * np.abs(W).max())
+        # a poisoned equilibrium is reported, not propagated silently
+        bad = W.copy()
+        bad[0, 10, 10] = np.nan
+        h.set_equilibrium(bad)
+        with pytest.raises(chfpe.ChfpeError) as e:
+            h.response1(wl.A, wl.C, 3, 1)
+        assert e.value.status == chfpe.EUNSTABLE
