@@ -137,6 +137,15 @@ def test_response1_one_mode_matches_oracle(prec, tol):
     assert _norm_err(got, want) < tol
 
 
+def _workload_optics(d):
+    """The optics of the named workloads: mu = q1 + q2 (two modes); water-like mu, Pi (three)."""
+    if d == 2:
+        mu = inputs.Optical(lin=(1.0, 1.0))
+        return mu, mu, mu
+    mu, Pi = inputs.three_mode_optics()
+    return mu, Pi, mu
+
+
 @pytest.mark.parametrize("prec,tol", [(64, 1e-10), (32, 1e-4)])
 @pytest.mark.parametrize("d,n,depth", [(2, [14, 12, 16, 13], 3), (3, [8, 7, 9, 8, 7, 9], 2)])
 def test_response2_matches_oracle(d, n, depth, prec, tol):
@@ -145,13 +154,31 @@ def test_response2_matches_oracle(d, n, depth, prec, tol):
     grid = inputs.default_grid(model, n, cut=12.0, nsigma=5.0)
     pb = oracle.Problem(model, grid, depth)
     Weq = ref.hierarchy_state(ref.boltzmann_sym(model, grid), pb.M)
-    mu, Pi = inputs.three_mode_optics()
+    A, B, C = _workload_optics(d)
     dt, nt1, nt2, stride = 0.004, 5, 4, 6
-    want = oracle.response2(pb, mu, Pi, mu, _rounded(Weq, prec), dt, nt1, nt2, stride)
+    want = oracle.response2(pb, A, B, C, _rounded(Weq, prec), dt, nt1, nt2, stride)
     with chfpe.Handle(model, grid, depth=depth, dt=dt, precision=prec, max_batch=3) as h:
         h.set_equilibrium(Weq)
-        got = h.response2(mu, Pi, mu, nt1, nt2, stride)
+        got = h.response2(A, B, C, nt1, nt2, stride)
     assert _norm_err(got, want) < tol
+
+
+def test_response2_strong_cancellation_fp64():
+    """Two modes with the water-like optics on a coarse 4D grid: the linear parts of mu and Pi
+    build branch states ~1e3 x larger than R2 that cancel in the observable, so FP32 rounding
+    (u = 6e-8) shows at ~2e-4 of max|R2| there; the FP64 path holds 1e-10."""
+    chfpe = _chfpe()
+    model = _model(2)
+    grid = inputs.default_grid(model, [14, 12, 16, 13], cut=12.0, nsigma=5.0)
+    pb = oracle.Problem(model, grid, 3)
+    Weq = ref.hierarchy_state(ref.boltzmann_sym(model, grid), pb.M)
+    mu, Pi = inputs.three_mode_optics()
+    dt, nt1, nt2, stride = 0.004, 5, 4, 6
+    want = oracle.response2(pb, mu, Pi, mu, Weq, dt, nt1, nt2, stride)
+    with chfpe.Handle(model, grid, depth=3, dt=dt, precision=64, max_batch=3) as h:
+        h.set_equilibrium(Weq)
+        got = h.response2(mu, Pi, mu, nt1, nt2, stride)
+    assert _norm_err(got, want) < 1e-10
 
 
 def test_response2_chunking_is_bitwise_invariant():
