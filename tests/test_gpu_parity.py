@@ -45,14 +45,18 @@ def _model(d):
                         gamma=(1.0, 1.5, 0.8), V_LL=(1.0, 0.7, 0.9), V_SL=(0.3, -0.4, 0.2))
 
 
-# ragged per-axis sizes: several 256-thread tiles plus a tail in every case
+# ragged per-axis sizes: several thread blocks plus a tail in every case; a fastest axis (p_d)
+# that is a multiple of 4 runs the vectorised stage kernel (float4 / double2), others the scalar
 CASES = [
     (1, [37, 45], 5),
+    (1, [37, 44], 5),
     (1, [64, 64], 8),
     (2, [9, 11, 13, 15], 4),
-    (2, [12, 10, 14, 9], 5),
+    (2, [9, 11, 13, 12], 4),
+    (2, [12, 10, 14, 8], 5),
     (3, [7, 8, 9, 7, 8, 9], 2),
-    (3, [7, 7, 8, 8, 7, 9], 3),
+    (3, [7, 8, 9, 7, 9, 8], 2),
+    (3, [7, 7, 8, 8, 7, 8], 3),
 ]
 
 
@@ -104,7 +108,7 @@ def test_insert_and_observe_match_oracle(d, n, depth, prec):
 
 
 @pytest.mark.parametrize("prec", [64, 32])
-@pytest.mark.parametrize("d,n,depth", [CASES[0], CASES[2], CASES[4]])
+@pytest.mark.parametrize("d,n,depth", [CASES[0], CASES[1], CASES[3], CASES[4], CASES[6], CASES[7]])
 def test_rk4_matches_oracle_and_batches_are_independent(d, n, depth, prec):
     model, grid, h, pb = _setup(d, n, depth, prec, max_batch=3)
     W = _rounded(inputs.random_state(grid, pb.M, seed=5, smooth=True), prec)
@@ -146,21 +150,26 @@ def _workload_optics(d):
     return mu, Pi, mu
 
 
-@pytest.mark.parametrize("prec,tol", [(64, 1e-10), (32, 1e-4)])
-@pytest.mark.parametrize("d,n,depth", [(2, [14, 12, 16, 13], 3), (3, [8, 7, 9, 8, 7, 9], 2)])
-def test_response2_matches_oracle(d, n, depth, prec, tol):
+@pytest.mark.parametrize("d,n,depth,dt,stride,nt", [
+    (2, [12, 11, 12, 12], 4, 0.01, 50, 4),     # vectorised stage kernel, t1, t2 <= 1.5
+    (2, [12, 12, 12, 13], 3, 0.01, 50, 4),     # scalar stage kernel
+    (3, [7, 7, 8, 8, 7, 8], 2, 0.004, 20, 3),  # water-like TRT optics, vectorised
+])
+def test_response2_matches_oracle(d, n, depth, dt, stride, nt):
+    """Both precisions against one oracle run on the float-rounded equilibrium: FP64 to 1e-10,
+    FP32 to 1e-4 of max|R2| (the response has developed: t1, t2 up to (nt-1) stride dt)."""
     chfpe = _chfpe()
     model = _model(d)
     grid = inputs.default_grid(model, n, cut=12.0, nsigma=5.0)
     pb = oracle.Problem(model, grid, depth)
-    Weq = ref.hierarchy_state(ref.boltzmann_sym(model, grid), pb.M)
+    Weq = _rounded(ref.hierarchy_state(ref.boltzmann_sym(model, grid), pb.M), 32)
     A, B, C = _workload_optics(d)
-    dt, nt1, nt2, stride = 0.004, 5, 4, 6
-    want = oracle.response2(pb, A, B, C, _rounded(Weq, prec), dt, nt1, nt2, stride)
-    with chfpe.Handle(model, grid, depth=depth, dt=dt, precision=prec, max_batch=3) as h:
-        h.set_equilibrium(Weq)
-        got = h.response2(A, B, C, nt1, nt2, stride)
-    assert _norm_err(got, want) < tol
+    want = oracle.response2(pb, A, B, C, Weq, dt, nt, nt, stride)
+    for prec, tol in ((64, 1e-10), (32, 1e-4)):
+        with chfpe.Handle(model, grid, depth=depth, dt=dt, precision=prec, max_batch=3) as h:
+            h.set_equilibrium(Weq)
+            got = h.response2(A, B, C, nt, nt, stride)
+        assert _norm_err(got, want) < tol, (prec, _norm_err(got, want))
 
 
 def test_response2_strong_cancellation_fp64():
@@ -239,3 +248,23 @@ def test_state_roundtrip_save_load_and_errors(tmp_path):
         with pytest.raises(chfpe.ChfpeError) as e:
             h.response1(wl.A, wl.C, 3, 1)
         assert e.value.status == chfpe.EUNSTABLE
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_vector_and_scalar_stage_kernels_agree(prec, monkeypatch):
+    """The vectorised stage kernel (p_d a multiple of the vector width) against the scalar one
+    on the same handle parameters: same arithmetic per cell, possibly another FMA grouping."""
+    model = _model(2)
+    grid = inputs.default_grid(model, [10, 9, 12, 16], cut=12.0, nsigma=5.0)
+    W = _rounded(inputs.random_state(grid, 15, seed=9, smooth=False), prec)
+    outs = []
+    for scalar in ("0", "1"):
+        monkeypatch.setenv("CHFPE_SCALAR_STAGE", scalar)
+        chfpe = _chfpe()
+        with chfpe.Handle(model, grid, depth=4, dt=0.004, precision=prec) as h:
+            x = torch.tensor(W, dtype=_dtype(prec), device="cuda")
+            y = torch.empty_like(x)
+            h.rhs_device(x.data_ptr(), y.data_ptr(), 1)
+            outs.append(y.double().cpu().numpy())
+    scale = np.abs(outs[0]).max()
+    assert np.abs(outs[0] - outs[1]).max() <= (1e-14 if prec == 64 else 1e-6) * scale
