@@ -237,19 +237,25 @@ def run_ours(args, rank, world, local, pg):
 
     peak, peak_kind = peaks()
     achieved = st["stage_bytes"] / (st["stage_ms"] / 1e3) / 1e9 if st["stage_ms"] > 0 else None
+    # DRAM bytes per launch from the committed ncu capture of this kernel: measured bytes per
+    # cell-stage times the cells of one branch-phase launch (nt1 states)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
     if os.path.exists(prof):
         try:
-            traffic = json.load(open(prof)).get("bytes_per_cell_stage_two_mode_32")
+            tj = json.load(open(prof))
+            per_cell = tj.get("bytes_per_cell_stage_two_mode_32")
+            if per_cell and tj.get("kernel") == "stage_vec_kernel<float,2,4,2,128,8>":
+                traffic = per_cell * nt1 * wl.cells
         except Exception:
             traffic = None
     roofline = {
-        "kernel": "stage_kernel<float,2,4>",
+        "kernel": "stage_vec_kernel<float,2,4,2,128,8>",
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
         "traffic": traffic,
         "algorithmic_bytes_per_cell_stage": ELEM_ACCESSES_PER_CELL_STEP * 4 / 4,
+        "traffic_per": "branch-phase launch (%d states), stage 2, from profiles/stage_kernel_traffic.json" % nt1,
         "stage_launches": st["stage_launches"],
         "avg_launch_ms": st["stage_ms"] / max(1, st["stage_launches"]),
     }
