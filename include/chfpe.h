@@ -149,6 +149,28 @@ chfpe_status chfpe_insert_device(chfpe_handle *h, const chfpe_optical *X, const 
 chfpe_status chfpe_observe_device(chfpe_handle *h, const chfpe_optical *C, const void *in,
                                   int batch, double *R_dev);
 
+/* ---- reduction without device allocations (no counterpart in the paper) ---------------------- */
+
+/* R_dev[b] = integral C(q) exp(-H/2kT) g^(0) of state b, b = 0..batch-1 -- the same quantity as
+ * chfpe_observe_device -- for callers that must not allocate device memory: programs that own a
+ * fixed device-memory budget and hand the library only pre-sized buffers, or latency-critical
+ * loops that cannot afford cudaMalloc's device synchronisation.  No handle is needed (creating
+ * one allocates).  Arguments: the model and grid as for chfpe_create, the hierarchy depth (it
+ * sets the state size M*P), precision 32 or 64 (float or double states), the observed operator
+ * C, `states` = device pointer to `batch` contiguous states (only member 0 is read), R_dev =
+ * caller-owned device memory of `batch` doubles, stream = cudaStream_t or NULL.  Asynchronous on
+ * `stream`; FP64 accumulation.  Nothing is allocated or freed: the per-block partial sums live in
+ * a fixed device array of 32768 doubles (256 KB, held on every GPU that loads the library until
+ * the process exits), so batch * min(512, ceil(P / 1024)) must not exceed 32768 (CHFPE_EINVAL
+ * with the limit otherwise).  The first call on each device looks the array's address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (different streams, no ordering) race.  Errors:
+ * CHFPE_EINVAL (arguments), CHFPE_ECUDA (launch or address lookup); message in
+ * chfpe_last_error(). */
+chfpe_status chfpe_observe_noalloc(const chfpe_model *model, const chfpe_grid *grid, int depth,
+                                   int precision, const chfpe_optical *C, const void *states,
+                                   int batch, double *R_dev, void *stream);
+
 /* ---- counters for measurement (no counterpart in the paper) ---------------------------------- */
 
 typedef struct {

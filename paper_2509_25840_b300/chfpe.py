@@ -98,6 +98,9 @@ def load(path: str = LIB_PATH):
         "chfpe_rk4_device": ([_H, _VP, ctypes.c_int, ctypes.c_long], S),
         "chfpe_insert_device": ([_H, ctypes.POINTER(chfpe_optical), _VP, _VP, ctypes.c_int], S),
         "chfpe_observe_device": ([_H, ctypes.POINTER(chfpe_optical), _VP, ctypes.c_int, _VP], S),
+        "chfpe_observe_noalloc": ([ctypes.POINTER(chfpe_model), ctypes.POINTER(chfpe_grid),
+                                   ctypes.c_int, ctypes.c_int, ctypes.POINTER(chfpe_optical),
+                                   _VP, ctypes.c_int, _VP, _VP], S),
         "chfpe_stats_reset": ([_H, ctypes.c_int], S),
         "chfpe_stats_get": ([_H, ctypes.POINTER(chfpe_stats)], S),
         "chfpe_last_error": ([], ctypes.c_char_p),
@@ -161,6 +164,16 @@ def make_optical(X: "inputs.Optical") -> chfpe_optical:
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(_DP)
+
+
+def observe_noalloc(model, grid, depth: int, precision: int, C, states_ptr: int, batch: int,
+                    R_ptr: int, stream: int | None = None):
+    """chfpe_observe_noalloc: the observable of `batch` device states into device doubles at
+    R_ptr, without any device allocation (fixed 256 KB reduction scratch inside the library)."""
+    m, g, c = make_model(model), make_grid(grid), make_optical(C)
+    _check(load().chfpe_observe_noalloc(ctypes.byref(m), ctypes.byref(g), int(depth),
+                                        int(precision), ctypes.byref(c), states_ptr, int(batch),
+                                        R_ptr, stream))
 
 
 class Handle:

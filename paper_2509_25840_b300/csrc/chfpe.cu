@@ -35,6 +35,11 @@ static chfpe_status fail(chfpe_status s, const std::string &msg) {
 
 extern "C" const char *chfpe_last_error(void) { return g_err.c_str(); }
 
+namespace chfpe {
+// lets entry points in other translation units report through chfpe_last_error()
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace chfpe
+
 // ------------------------------------------------------------------------------------------
 // handle
 // ------------------------------------------------------------------------------------------

@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(NT) observe_partial_kernel(const ObserveArgs a
 }
 
 // out[j * out_stride] = scale * sum_b partial[j][b], fixed order; one warp per state
-__global__ void observe_finish_kernel(const double *partial, int nblk, int batch, double scale,
+static __global__ void observe_finish_kernel(const double *partial, int nblk, int batch, double scale,
                                       double *out, long long out_stride) {
     const int j = blockIdx.x;
     if (j >= batch) return;
@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(NT) boltzmann_kernel(double *g0, int P, int Pp
     if (threadIdx.x == 0) partial[blockIdx.x] = sum;
 }
 
-__global__ void scale_by_sum_kernel(double *g, long long n, const double *partial, int nblk,
+static __global__ void scale_by_sum_kernel(double *g, long long n, const double *partial, int nblk,
                                     double vol) {
     // g *= 1 / (vol * sum partial), the sum taken in fixed order by every thread
     double Z = 0.0;
