@@ -82,8 +82,14 @@ typedef struct {
     int depth;          /* hierarchy truncation: members with n_1+..+n_d <= depth              */
     int precision;      /* 32: float state and arithmetic; 64: double (check build)            */
     double dt;          /* RK4 time step; create fails if dt exceeds the stability bound       */
-    int max_batch;      /* most states propagated together by one launch (response branches)  */
+    int max_batch;      /* most states propagated together by one launch (response branches);  */
+                        /* 0 = no branch arenas (chfpe_response2 then unavailable)             */
     void *stream;       /* cudaStream_t to issue work on; NULL = a stream the handle creates   */
+    int bf16_tier;      /* T >= 1: members with n_1+..+n_d >= T stored as bf16 (FP32 compute;  */
+                        /* precision 32; compiled for 2 modes / depth 4 / T = 3 and 3 modes /  */
+                        /* depth 2 / T = 2); <= 0: off.  Device buffers passed to the          */
+                        /* *_device calls then use the mixed layout: the FP32 members first,   */
+                        /* then the bf16 members, each [grid] as above                          */
 } chfpe_options;
 
 /* Create a handle for one model on one grid.  Validates the structs, builds the coefficient
@@ -130,6 +136,28 @@ chfpe_status chfpe_response2(chfpe_handle *h, const chfpe_optical *A, const chfp
  * W_eq to a file and Sec. IV C reads it back. */
 chfpe_status chfpe_save_equilibrium(const chfpe_handle *h, const char *path);
 chfpe_status chfpe_load_equilibrium(chfpe_handle *h, const char *path);
+
+/* ---- batches: many instances (models and grids) advanced together (BASELINE sweep config) -- */
+
+/* Create a batch of n instances (models[i], grids[i]) sharing one set of options (same number of
+ * modes, depth, precision, bf16_tier; max_batch is ignored).  Every RK4 stage of every instance is
+ * one launch over a work list of (instance, tile) items.  One step of the batch is nsub substeps
+ * of dt / nsub, nsub the smallest power of two keeping every instance inside the RK4 stability
+ * bound (A15: a stiff instance lowers the step of the batch instead of failing).  Instance states
+ * live in batch-owned arenas; destroy the batch with chfpe_destroy (it destroys the instances). */
+chfpe_status chfpe_create_batch(int n, const chfpe_model *models, const chfpe_grid *grids,
+                                const chfpe_options *opts, chfpe_handle **out);
+/* Borrow instance i of a batch (owned by the batch: do not destroy) for per-instance calls:
+ * equilibrate, set/get equilibrium or state, response1, propagate. */
+chfpe_status chfpe_batch_instance(chfpe_handle *batch, int i, chfpe_handle **inst);
+/* chfpe_equilibrate on every instance (max_steps and check_every in batch steps); residuals[i]
+ * (may be NULL) receives instance i's last residual. */
+chfpe_status chfpe_batch_equilibrate(chfpe_handle *batch, long max_steps, double tol,
+                                     long check_every, double *residuals);
+/* R1 (Eq. 1Dresponse) of every instance from its equilibrium: R[i * nt + k] (host, caller-owned),
+ * t = k stride dt, all instances advanced by the same fused launches. */
+chfpe_status chfpe_batch_response1(chfpe_handle *batch, const chfpe_optical *A,
+                                   const chfpe_optical *C, int nt, int stride, double *R);
 
 /* Sizes of the handle: members M and points per member P (states are M*P values). */
 chfpe_status chfpe_sizes(const chfpe_handle *h, int *members, long *points);

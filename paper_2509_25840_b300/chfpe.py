@@ -49,7 +49,7 @@ class chfpe_grid(ctypes.Structure):
 
 class chfpe_options(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int), ("precision", ctypes.c_int), ("dt", ctypes.c_double),
-                ("max_batch", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("max_batch", ctypes.c_int), ("stream", ctypes.c_void_p), ("bf16_tier", ctypes.c_int)]
 
 
 class chfpe_stats(ctypes.Structure):
@@ -101,6 +101,12 @@ def load(path: str = LIB_PATH):
         "chfpe_observe_noalloc": ([ctypes.POINTER(chfpe_model), ctypes.POINTER(chfpe_grid),
                                    ctypes.c_int, ctypes.c_int, ctypes.POINTER(chfpe_optical),
                                    _VP, ctypes.c_int, _VP, _VP], S),
+        "chfpe_create_batch": ([ctypes.c_int, ctypes.POINTER(chfpe_model), ctypes.POINTER(chfpe_grid),
+                                ctypes.POINTER(chfpe_options), ctypes.POINTER(_H)], S),
+        "chfpe_batch_instance": ([_H, ctypes.c_int, ctypes.POINTER(_H)], S),
+        "chfpe_batch_equilibrate": ([_H, ctypes.c_long, ctypes.c_double, ctypes.c_long, _DP], S),
+        "chfpe_batch_response1": ([_H, ctypes.POINTER(chfpe_optical), ctypes.POINTER(chfpe_optical),
+                                   ctypes.c_int, ctypes.c_int, _DP], S),
         "chfpe_stats_reset": ([_H, ctypes.c_int], S),
         "chfpe_stats_get": ([_H, ctypes.POINTER(chfpe_stats)], S),
         "chfpe_last_error": ([], ctypes.c_char_p),
@@ -180,11 +186,11 @@ class Handle:
     """One model on one grid: owns the device arenas of libchfpe."""
 
     def __init__(self, model, grid, depth: int, dt: float, precision: int = 32,
-                 max_batch: int = 1, stream: int | None = None):
+                 max_batch: int = 1, stream: int | None = None, bf16_tier: int = 0):
         lib = load()
         self._m, self._g = make_model(model), make_grid(grid)
         self._o = chfpe_options(depth=int(depth), precision=int(precision), dt=float(dt),
-                                max_batch=int(max_batch), stream=stream)
+                                max_batch=int(max_batch), stream=stream, bf16_tier=int(bf16_tier))
         h = _H()
         _check(lib.chfpe_create(ctypes.byref(self._m), ctypes.byref(self._g),
                                 ctypes.byref(self._o), ctypes.byref(h)))
@@ -196,10 +202,25 @@ class Handle:
         self.precision = int(precision)
         self.max_batch = int(max_batch)
 
+    @classmethod
+    def _borrowed(cls, h, grid, precision: int):
+        """Wrap an instance handle owned by a batch (closing the wrapper does not destroy it)."""
+        self = cls.__new__(cls)
+        self._h = h
+        self._owner = False
+        M, P = ctypes.c_int(), ctypes.c_long()
+        _check(load().chfpe_sizes(h, ctypes.byref(M), ctypes.byref(P)))
+        self.members, self.points = M.value, P.value
+        self.shape = tuple(grid.nq) + tuple(grid.np)
+        self.precision = int(precision)
+        self.max_batch = 0
+        return self
+
     # -- lifetime -------------------------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None):
-            load().chfpe_destroy(self._h)
+            if getattr(self, "_owner", True):
+                load().chfpe_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -297,3 +318,51 @@ class Handle:
         st = chfpe_stats()
         _check(load().chfpe_stats_get(self._h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in chfpe_stats._fields_}
+
+
+class Batch(Handle):
+    """chfpe_create_batch: n instances (models, grids) advanced together by one launch per RK4
+    stage; instance(i) gives the borrowed per-instance handle."""
+
+    def __init__(self, models, grids, depth: int, dt: float, precision: int = 32,
+                 stream: int | None = None, bf16_tier: int = 0):
+        lib = load()
+        n = len(models)
+        self._ms = (chfpe_model * n)(*[make_model(m) for m in models])
+        self._gs = (chfpe_grid * n)(*[make_grid(g) for g in grids])
+        self._o = chfpe_options(depth=int(depth), precision=int(precision), dt=float(dt),
+                                max_batch=0, stream=stream, bf16_tier=int(bf16_tier))
+        h = _H()
+        _check(lib.chfpe_create_batch(n, self._ms, self._gs, ctypes.byref(self._o), ctypes.byref(h)))
+        self._h = h
+        self._owner = True
+        self.n = n
+        self.grids = list(grids)
+        self.precision = int(precision)
+        self._inst = [None] * n
+
+    def instance(self, i: int) -> Handle:
+        if self._inst[i] is None:
+            h = _H()
+            _check(load().chfpe_batch_instance(self._h, int(i), ctypes.byref(h)))
+            self._inst[i] = Handle._borrowed(h, self.grids[i], self.precision)
+        return self._inst[i]
+
+    def equilibrate_all(self, max_steps: int, tol: float, check_every: int = 100) -> np.ndarray:
+        r = np.zeros(self.n)
+        _check(load().chfpe_batch_equilibrate(self._h, int(max_steps), float(tol), int(check_every),
+                                              _dptr(r)))
+        return r
+
+    def response1_all(self, A, C, nt: int, stride: int) -> np.ndarray:
+        R = np.empty((self.n, nt))
+        a, c = make_optical(A), make_optical(C)
+        _check(load().chfpe_batch_response1(self._h, ctypes.byref(a), ctypes.byref(c), int(nt),
+                                            int(stride), _dptr(R)))
+        return R
+
+    def close(self):
+        for w in getattr(self, "_inst", []) or []:
+            if w is not None:
+                w._h = None
+        super().close()

@@ -57,8 +57,10 @@ struct chfpe_handle {
     double dt = 0.0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    size_t esize = 4;           // bytes per state value
-    long long state = 0;        // values per state
+    size_t esize = 4;           // bytes per FP32/FP64 state value
+    long long state = 0;        // values per state (M * P)
+    int M32 = 0;                // members stored in the handle precision; the rest (deep tiers) bf16
+    long long state_bytes = 0;  // bytes per state: M32 P esize + (M - M32) P 2
 
     // coefficient tables (device)
     double *U_d = nullptr;      // [NQ] U(q)
@@ -80,21 +82,33 @@ struct chfpe_handle {
     int partial_cap = 0;
     double *dR = nullptr;                                  // device response buffer
     size_t dR_cap = 0;
+    int *counter = nullptr;                                // device sample counter (graphs)
+    int use_graphs = -1;                                   // -1: decide by size; 0 off; 1 on
 
     // measurement counters
     long long launches = 0, stage_launches = 0;
     double stage_bytes = 0.0, cell_updates = 0.0;
     bool time_stages = false;
-    bool force_scalar = false;          // CHFPE_SCALAR_STAGE=1: always the scalar stage kernel
+    bool force_scalar = false;          // CHFPE_SCALAR_STAGE=1: one point per thread (V = 1)
     std::vector<cudaEvent_t> ev;        // pairs (start, stop) of timed bursts
     size_t ev_used = 0;
+
+    // instance of a batch: its state arenas are slices of the batch's arenas
+    bool borrowed_arenas = false;
+    // batch (chfpe_create_batch): instances share the stream; one launch per RK4 stage
+    std::vector<chfpe_handle *> inst;
+    std::vector<long long> inst_off;    // byte offset of each instance in the batch arenas
+    int nsub = 1;                       // RK4 substeps per requested step (dt / nsub per step)
+    void *d_geo = nullptr;              // InstGeo<T>[n]
+    int2 *d_work_vec = nullptr, *d_work_sc = nullptr;
+    int nwork_vec = 0, nwork_sc = 0;
+    double cells_total = 0.0;
 };
 
 template <typename T>
-static StageArgs<T> stage_args(const chfpe_handle *h) {
-    StageArgs<T> a;
+static Geo<T> geo_of(const chfpe_handle *h) {
+    Geo<T> a;
     memset(&a, 0, sizeof(a));
-    a.state = h->state;
     a.P = h->P;
     for (int i = 0; i < 6; ++i) { a.n[i] = h->n[i]; a.st[i] = h->st[i]; }
     a.Pp = h->Pp;
@@ -119,23 +133,66 @@ static StageArgs<T> stage_args(const chfpe_handle *h) {
     return a;
 }
 
+// Stage arguments for arrays of element type T: the handle's own arenas use its storage layout
+// (bf16 deep tiers when enabled); FP64 arrays (equilibration) are always plain.
+template <typename T>
+static StageArgs<T> stage_args(const chfpe_handle *h) {
+    StageArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.state_bytes = sizeof(T) == 8 ? h->state * 8 : h->state_bytes;
+    a.g = geo_of<T>(h);
+    return a;
+}
+
 // Vectorised stage kernel shape: two consecutive p_d points per thread (float2 / double2), 128
 // threads per block, registers capped so that 8 blocks (32 warps) fit on an SM for hierarchies
 // of up to 15 members (4 blocks beyond).  Measured on the 32^4 x 15 workload: occupancy beats
 // per-thread reuse here (float4 at 8 warps/SM: 1.6 TB/s; float2 at 32 warps/SM: 2.0 TB/s).
 constexpr int kVec = 2;
 
-template <typename T, int D, int DEPTH>
-static void launch_stage_t(const StageArgs<T> &a, int batch, bool vec, cudaStream_t s) {
+// BF16 storage of deep tiers is compiled for these (d, depth, first bf16 member) combinations
+// (FP32 path only): two modes, depth 4, tiers 3-4 (9 of 15 members); three modes, depth 2,
+// tier 2 (6 of 10 members).
+static int bf16_m32(int d, int depth, int tier) {
+    if (d == 2 && depth == 4 && tier == 3) return 6;
+    if (d == 3 && depth == 2 && tier == 2) return 4;
+    return -1;
+}
+
+template <typename T, int D, int DEPTH, int M32>
+static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, cudaStream_t s) {
     constexpr int M = member_count(D, DEPTH);
     constexpr int MINB = (sizeof(T) == 4 && M <= 15) ? 8 : 4;
     if (vec) {
-        const int nthr = a.P / kVec;
-        stage_vec_kernel<T, D, DEPTH, kVec, 128, MINB>
+        const int nthr = a.g.P / kVec;
+        stage_vec_kernel<T, D, DEPTH, kVec, 128, MINB, M32>
             <<<dim3((nthr + 127) / 128, batch), 128, 0, s>>>(a);
     } else {
-        stage_kernel<T, D, DEPTH><<<dim3((a.P + 255) / 256, batch), 256, 0, s>>>(a);
+        stage_vec_kernel<T, D, DEPTH, 1, 128, 4, M32>
+            <<<dim3((a.g.P + 127) / 128, batch), 128, 0, s>>>(a);
     }
+}
+
+template <typename T, int D, int DEPTH>
+static bool launch_stage_t(const StageArgs<T> &a, int batch, bool vec, int M32, cudaStream_t s) {
+    constexpr int M = member_count(D, DEPTH);
+    if (M32 == M) {
+        launch_stage_m<T, D, DEPTH, M>(a, batch, vec, s);
+        return true;
+    }
+    if constexpr (sizeof(T) == 4 && D == 2 && DEPTH == 4) {
+        if (M32 == 6) {
+            launch_stage_m<T, D, DEPTH, 6>(a, batch, vec, s);
+            return true;
+        }
+    }
+    if constexpr (sizeof(T) == 4 && D == 3 && DEPTH == 2) {
+        if (M32 == 4) {
+            launch_stage_m<T, D, DEPTH, 4>(a, batch, vec, s);
+            return true;
+        }
+    }
+    return false;
 }
 
 static bool aligned16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
@@ -146,7 +203,8 @@ static bool launch_stage(const chfpe_handle *h, const StageArgs<T> &a, int batch
     const bool vec = (h->n[2 * h->d - 1] % kVec == 0) && aligned16(a.in) && aligned16(a.y) &&
                      aligned16(a.out) && !h->force_scalar;
 #define CASE(D_, K_) \
-    case (D_ * 16 + K_): launch_stage_t<T, D_, K_>(a, batch, vec, s); return true;
+    case (D_ * 16 + K_): return launch_stage_t<T, D_, K_>(a, batch, vec, m32, s);
+    const int m32 = sizeof(T) == 8 ? h->M : h->M32;
     switch (h->d * 16 + h->depth) {
         CASE(1, 0) CASE(1, 1) CASE(1, 2) CASE(1, 3) CASE(1, 4) CASE(1, 5) CASE(1, 6) CASE(1, 7)
         CASE(1, 8)
@@ -162,9 +220,9 @@ template <typename T>
 static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *out, double c,
                           int batch) {
     StageArgs<T> a = stage_args<T>(h);
-    a.in = (const T *)in;
-    a.y = (const T *)y;
-    a.out = (T *)out;
+    a.in = (const char *)in;
+    a.y = (const char *)y;
+    a.out = (char *)out;
     a.c = (T)c;
     if (!launch_stage<T>(h, a, batch)) return fail(CHFPE_EINVAL, "unsupported (d, depth)");
     CK(cudaGetLastError());
@@ -203,7 +261,8 @@ static chfpe_status rk4(chfpe_handle *h, void *y, void *za, void *zb, int batch,
     h->cell_updates += cells;
     if (h->time_stages) {
         h->stage_launches += 4 * nsteps;
-        h->stage_bytes += cells * 11.0 * sizeof(T);
+        // 11 element accesses per cell and step at the stored element size (bf16 deep tiers)
+        h->stage_bytes += (double)nsteps * batch * (double)h->state_bytes * 11.0;
     }
     return CHFPE_OK;
 }
@@ -349,13 +408,13 @@ static int observe_blocks(const chfpe_handle *h) {
 }
 
 static chfpe_status observe(chfpe_handle *h, const void *states, int batch, double *out,
-                            long long out_stride) {
+                            long long out_stride, const int *counter = nullptr) {
     const int nblk = observe_blocks(h);
     if ((long long)nblk * batch > h->partial_cap) return fail(CHFPE_EINVAL, "batch too large for reduction scratch");
     ObserveArgs a;
     memset(&a, 0, sizeof(a));
     a.in = states;
-    a.state = h->state;
+    a.state_bytes = h->state_bytes;
     a.P = h->P;
     a.Pp = h->Pp;
     a.d = h->d;
@@ -373,7 +432,12 @@ static chfpe_status observe(chfpe_handle *h, const void *states, int batch, doub
     CK(cudaGetLastError());
     double vol = 1.0;
     for (int ax = 0; ax < 2 * h->d; ++ax) vol *= h->h[ax];
-    observe_finish_kernel<<<batch, 32, 0, h->stream>>>(h->partial, nblk, batch, vol, out, out_stride);
+    if (counter)
+        observe_finish_counter_kernel<<<batch, 32, 0, h->stream>>>(h->partial, nblk, batch, vol,
+                                                                   out, out_stride, counter);
+    else
+        observe_finish_kernel<<<batch, 32, 0, h->stream>>>(h->partial, nblk, batch, vol, out,
+                                                           out_stride);
     CK(cudaGetLastError());
     h->launches += 2;
     return CHFPE_OK;
@@ -388,12 +452,13 @@ static chfpe_status insert_t(chfpe_handle *h, const chfpe_optical *X, const void
                              long long in_state, void *out, int batch) {
     InsertArgs<T> a;
     memset(&a, 0, sizeof(a));
-    a.in = (const T *)in;
-    a.out = (T *)out;
+    a.in = (const char *)in;
+    a.out = (char *)out;
     a.in_state = in_state;
-    a.out_state = h->state;
+    a.out_state = h->state_bytes;
     a.P = h->P;
     a.M = h->M;
+    a.M32 = h->M32;
     a.d = h->d;
     for (int i = 0; i < 6; ++i) { a.n[i] = h->n[i]; a.st[i] = h->st[i]; }
     for (int s = 0; s < h->d; ++s) {
@@ -480,7 +545,7 @@ static chfpe_status validate(const chfpe_model *m, const chfpe_grid *g, const ch
         return fail(CHFPE_EINVAL, "depth out of range (d=1: <=8, d=2: <=5, d=3: <=3)");
     if (o->precision != 32 && o->precision != 64) return fail(CHFPE_EINVAL, "precision must be 32 or 64");
     if (!(o->dt > 0) || !is_fin(o->dt)) return fail(CHFPE_EINVAL, "dt must be positive");
-    if (o->max_batch < 1 || o->max_batch > 65535) return fail(CHFPE_EINVAL, "max_batch must be in 1..65535");
+    if (o->max_batch < 0 || o->max_batch > 65535) return fail(CHFPE_EINVAL, "max_batch must be in 0..65535");
     long long P = 1;
     for (int s = 0; s < m->nmodes; ++s) P *= (long long)g->nq[s] * g->np[s];
     const long long M = member_count(m->nmodes, o->depth);
@@ -504,8 +569,11 @@ static T *dalloc(size_t n, chfpe_status *st) {
 extern "C" void chfpe_destroy(chfpe_handle *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (chfpe_handle *c : h->inst) chfpe_destroy(c);
+    if (h->borrowed_arenas) h->cy = h->ca = h->cb = h->eq = nullptr;
     void *ptrs[] = {h->U_d, h->F_d, h->F_f, h->wp, h->CWq, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
-                    h->cy, h->ca, h->cb, h->by, h->ba, h->bb, h->eq, h->stage64, h->partial, h->dR};
+                    h->cy, h->ca, h->cb, h->by, h->ba, h->bb, h->eq, h->stage64, h->partial, h->dR,
+                    h->counter, h->d_geo, h->d_work_vec, h->d_work_sc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -513,13 +581,14 @@ extern "C" void chfpe_destroy(chfpe_handle *h) {
     delete h;
 }
 
-extern "C" chfpe_status chfpe_create(const chfpe_model *model, const chfpe_grid *grid,
-                                     const chfpe_options *opts, chfpe_handle **out) {
+static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid,
+                                const chfpe_options *opts, bool borrowed, chfpe_handle **out) {
     if (!out) return fail(CHFPE_EINVAL, "out is null");
     *out = nullptr;
     chfpe_status st = validate(model, grid, opts);
     if (st) return st;
     chfpe_handle *h = new chfpe_handle();
+    h->borrowed_arenas = borrowed;
     h->model = *model;
     h->grid = *grid;
     h->opts = *opts;
@@ -545,6 +614,17 @@ extern "C" chfpe_status chfpe_create(const chfpe_model *model, const chfpe_grid 
     h->NQ = 1;
     for (int s = 0; s < d; ++s) { h->Pp *= h->n[d + s]; h->NQ *= h->n[s]; }
     h->state = (long long)h->M * h->P;
+    h->M32 = h->M;
+    if (opts->bf16_tier > 0) {
+        const int m32 = bf16_m32(h->d, h->depth, opts->bf16_tier);
+        if (h->prec != 32 || m32 < 0) {
+            delete h;
+            return fail(CHFPE_EINVAL, "bf16_tier is supported for precision 32 with (modes 2, depth "
+                                      "4, tier 3) and (modes 3, depth 2, tier 2)");
+        }
+        h->M32 = m32;
+    }
+    h->state_bytes = (long long)h->M32 * h->P * h->esize + (long long)(h->M - h->M32) * h->P * 2;
     {
         const char *env = getenv("CHFPE_SCALAR_STAGE");
         h->force_scalar = env && env[0] == '1';
@@ -583,10 +663,19 @@ extern "C" chfpe_status chfpe_create(const chfpe_model *model, const chfpe_grid 
     h->partial_cap = observe_blocks(h) * std::max(opts->max_batch, 1);
     if (h->partial_cap < 4096) h->partial_cap = 4096;
     h->partial = dalloc<double>(h->partial_cap, &st);
+    h->counter = dalloc<int>(1, &st);
+    {
+        const char *eg = getenv("CHFPE_GRAPHS");
+        if (eg) h->use_graphs = atoi(eg);
+    }
+    (void)sb;
+    const size_t sbytes = (size_t)h->state_bytes;
     void **arenas[] = {&h->cy, &h->ca, &h->cb, &h->eq};
-    for (void **p : arenas) if (!st) *p = (void *)dalloc<char>(sb * h->esize, &st);
+    if (!borrowed)
+        for (void **p : arenas) if (!st) *p = (void *)dalloc<char>(sbytes, &st);
     void **barenas[] = {&h->by, &h->ba, &h->bb};
-    for (void **p : barenas) if (!st) *p = (void *)dalloc<char>(sb * h->esize * opts->max_batch, &st);
+    for (void **p : barenas)
+        if (!st && opts->max_batch > 0) *p = (void *)dalloc<char>(sbytes * opts->max_batch, &st);
     if (st) { chfpe_destroy(h); return st; }
 
     // coefficient tables
@@ -616,6 +705,11 @@ extern "C" chfpe_status chfpe_create(const chfpe_model *model, const chfpe_grid 
     return CHFPE_OK;
 }
 
+extern "C" chfpe_status chfpe_create(const chfpe_model *model, const chfpe_grid *grid,
+                                     const chfpe_options *opts, chfpe_handle **out) {
+    return create_impl(model, grid, opts, false, out);
+}
+
 extern "C" chfpe_status chfpe_sizes(const chfpe_handle *h, int *members, long *points) {
     if (!h) return fail(CHFPE_EINVAL, "null handle");
     if (members) *members = h->M;
@@ -643,7 +737,8 @@ static chfpe_status upload(chfpe_handle *h, const double *host, void *dst) {
         chfpe_status st = ensure_stage64(h);
         if (st) return st;
         CK(cudaMemcpyAsync(h->stage64, host, n * 8, cudaMemcpyHostToDevice, h->stream));
-        convert_kernel<double, float><<<1184, 256, 0, h->stream>>>(h->stage64, (float *)dst, n);
+        to_mixed_kernel<float><<<1184, 256, 0, h->stream>>>(h->stage64, (char *)dst,
+                                                            (long long)h->M32 * h->P, n);
         CK(cudaGetLastError());
     }
     CK(cudaStreamSynchronize(h->stream));
@@ -659,7 +754,8 @@ static chfpe_status download(const chfpe_handle *hc, const void *src, double *ho
     } else {
         chfpe_status st = ensure_stage64(h);
         if (st) return st;
-        convert_kernel<float, double><<<1184, 256, 0, h->stream>>>((const float *)src, h->stage64, n);
+        from_mixed_kernel<float><<<1184, 256, 0, h->stream>>>((const char *)src, h->stage64,
+                                                              (long long)h->M32 * h->P, n);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(host, h->stage64, n * 8, cudaMemcpyDeviceToHost, h->stream));
     }
@@ -773,7 +869,8 @@ extern "C" chfpe_status chfpe_equilibrate(chfpe_handle *h, long max_steps, doubl
     if (h->prec == 64) {
         e = cudaMemcpyAsync(h->eq, y, n * 8, cudaMemcpyDeviceToDevice, h->stream);
     } else {
-        convert_kernel<double, float><<<1184, 256, 0, h->stream>>>(y, (float *)h->eq, n);
+        to_mixed_kernel<float><<<1184, 256, 0, h->stream>>>(y, (char *)h->eq,
+                                                            (long long)h->M32 * h->P, n);
         e = cudaGetLastError();
     }
     if (!e) e = cudaStreamSynchronize(h->stream);
@@ -807,6 +904,60 @@ static chfpe_status finish_response(chfpe_handle *h, double *R, size_t n) {
     return CHFPE_OK;
 }
 
+// Sampling loop shared by R1 and the R2 branch phase: for k = 0..nsamples-1 observe the states
+// into out[j * out_stride + k], then (except after the last sample) advance them `stride` RK4 steps.
+// When the states are small enough that launch overhead matters, one interval (the stride RK4
+// steps followed by the observation) is captured once as a CUDA graph and replayed, the output
+// slot advancing through a device-side counter.
+static chfpe_status sampled_propagation(chfpe_handle *h, void *y, void *za, void *zb, int batch,
+                                        int nsamples, int stride, double *out,
+                                        long long out_stride) {
+    chfpe_status st;
+    const double cells = (double)batch * (double)h->state;
+    bool graphs = h->use_graphs == 1 || (h->use_graphs < 0 && cells * (4.0 * stride) < 2e9 &&
+                                         stride > 0 && nsamples > 2 && !h->time_stages);
+    if ((st = observe(h, y, batch, out, out_stride))) return st;
+    if (nsamples == 1) return CHFPE_OK;
+    if (!graphs) {
+        for (int k = 1; k < nsamples; ++k) {
+            if ((st = rk4_any(h, y, za, zb, batch, stride))) return st;
+            if ((st = observe(h, y, batch, out + k, out_stride))) return st;
+        }
+        return CHFPE_OK;
+    }
+    const int one = 1;
+    CK(cudaMemcpyAsync(h->counter, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const long long launches0 = h->launches;
+    const double cells0 = h->cell_updates;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    st = rk4_any(h, y, za, zb, batch, stride);
+    if (!st) st = observe(h, y, batch, out, out_stride, h->counter);
+    if (!st) {
+        counter_add_kernel<<<1, 1, 0, h->stream>>>(h->counter, 1);
+        ++h->launches;
+    }
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) return fail(CHFPE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(CHFPE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    const long long per_launch = h->launches - launches0;
+    const double per_cells = h->cell_updates - cells0;
+    for (int k = 1; k < nsamples; ++k) {
+        e = cudaGraphLaunch(exec, h->stream);
+        if (e != cudaSuccess) break;
+    }
+    // counters: the capture pass counted one interval; the replays ran nsamples - 1 of them
+    h->launches += per_launch * (nsamples - 2);
+    h->cell_updates += per_cells * (nsamples - 2);
+    cudaGraphExecDestroy(exec);
+    if (e != cudaSuccess) return fail(CHFPE_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    return CHFPE_OK;
+}
+
 extern "C" chfpe_status chfpe_response1(chfpe_handle *h, const chfpe_optical *A,
                                         const chfpe_optical *C, int nt, int stride, double *R) {
     if (!h || !A || !C || !R) return fail(CHFPE_EINVAL, "null argument");
@@ -816,10 +967,7 @@ extern "C" chfpe_status chfpe_response1(chfpe_handle *h, const chfpe_optical *A,
     if ((st = ensure_dR(h, nt))) return st;
     if ((st = set_observable(h, C))) return st;
     if ((st = insert(h, A, h->eq, 0, h->cy, 1))) return st;
-    for (int k = 0; k < nt; ++k) {
-        if ((st = observe(h, h->cy, 1, h->dR + k, 1))) return st;
-        if (k + 1 < nt && (st = rk4_any(h, h->cy, h->ca, h->cb, 1, stride))) return st;
-    }
+    if ((st = sampled_propagation(h, h->cy, h->ca, h->cb, 1, nt, stride, h->dR, 1))) return st;
     h->have_state = true;
     return finish_response(h, R, nt);
 }
@@ -830,6 +978,7 @@ extern "C" chfpe_status chfpe_response2(chfpe_handle *h, const chfpe_optical *A,
     if (!h || !A || !B || !C || !R) return fail(CHFPE_EINVAL, "null argument");
     if (nt1 < 1 || nt2 < 1 || stride < 0) return fail(CHFPE_EINVAL, "nt1, nt2 >= 1, stride >= 0");
     if (!h->have_eq) return fail(CHFPE_ESTATE, "no equilibrium: call chfpe_equilibrate or chfpe_set_equilibrium");
+    if (h->opts.max_batch < 1) return fail(CHFPE_EINVAL, "handle created with max_batch = 0: no branch arenas");
     chfpe_status st;
     const size_t total = (size_t)nt1 * nt2;
     if ((st = ensure_dR(h, total))) return st;
@@ -837,7 +986,7 @@ extern "C" chfpe_status chfpe_response2(chfpe_handle *h, const chfpe_optical *A,
     // t1 chain
     if ((st = insert(h, A, h->eq, 0, h->cy, 1))) return st;
     const int cap = h->opts.max_batch;
-    const size_t sbytes = (size_t)h->state * h->esize;
+    const size_t sbytes = (size_t)h->state_bytes;
     for (int i0 = 0; i0 < nt1; i0 += cap) {
         const int nb = std::min(cap, nt1 - i0);
         // spawn the branches of this chunk along the chain
@@ -846,10 +995,9 @@ extern "C" chfpe_status chfpe_response2(chfpe_handle *h, const chfpe_optical *A,
             if (i0 + c + 1 < nt1 && (st = rk4_any(h, h->cy, h->ca, h->cb, 1, stride))) return st;
         }
         // advance the chunk's branches in lockstep
-        for (int j = 0; j < nt2; ++j) {
-            if ((st = observe(h, h->by, nb, h->dR + (size_t)i0 * nt2 + j, nt2))) return st;
-            if (j + 1 < nt2 && (st = rk4_any(h, h->by, h->ba, h->bb, nb, stride))) return st;
-        }
+        if ((st = sampled_propagation(h, h->by, h->ba, h->bb, nb, nt2, stride,
+                                      h->dR + (size_t)i0 * nt2, nt2)))
+            return st;
     }
     h->have_state = true;
     return finish_response(h, R, total);
@@ -880,7 +1028,7 @@ extern "C" chfpe_status chfpe_rk4_device(chfpe_handle *h, void *states, int batc
 extern "C" chfpe_status chfpe_insert_device(chfpe_handle *h, const chfpe_optical *X, const void *in,
                                             void *out, int batch) {
     if (!h || !X || !in || !out || batch < 1 || batch > 65535) return fail(CHFPE_EINVAL, "bad argument");
-    chfpe_status st = insert(h, X, in, h->state, out, batch);
+    chfpe_status st = insert(h, X, in, h->state_bytes, out, batch);
     if (st) return st;
     CK(cudaStreamSynchronize(h->stream));
     return CHFPE_OK;
@@ -988,4 +1136,285 @@ extern "C" chfpe_status chfpe_stats_get(chfpe_handle *h, chfpe_stats *out) {
     out->stage_bytes = h->stage_bytes;
     out->cell_updates = h->cell_updates;
     return CHFPE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// batches of instances with different grids and parameters (parameter sweeps)
+// ------------------------------------------------------------------------------------------
+
+// spectral-radius bound of one (model, grid, depth) without creating a handle
+static double bound_for(const chfpe_model *model, const chfpe_grid *grid, int depth) {
+    chfpe_handle t;
+    t.model = *model;
+    t.d = model->nmodes;
+    t.depth = depth;
+    const int d = t.d;
+    for (int s = 0; s < d; ++s) {
+        t.n[s] = grid->nq[s];
+        t.n[d + s] = grid->np[s];
+        t.lo[s] = grid->qmin[s];
+        t.lo[d + s] = grid->pmin[s];
+        t.h[s] = (grid->qmax[s] - grid->qmin[s]) / (grid->nq[s] - 1);
+        t.h[d + s] = (grid->pmax[s] - grid->pmin[s]) / (grid->np[s] - 1);
+    }
+    t.NQ = 1;
+    for (int s = 0; s < d; ++s) t.NQ *= t.n[s];
+    return spectral_bound(&t);
+}
+
+template <typename T, int D, int DEPTH, int M32>
+static void launch_batch_m(const chfpe_handle *b, const BatchStageArgs<T> &a0) {
+    constexpr int M = member_count(D, DEPTH);
+    constexpr int MINB = (sizeof(T) == 4 && M <= 15) ? 8 : 4;
+    BatchStageArgs<T> a = a0;
+    if (b->nwork_vec) {
+        a.work = b->d_work_vec;
+        stage_batch_kernel<T, D, DEPTH, kVec, 128, MINB, M32><<<b->nwork_vec, 128, 0, b->stream>>>(a);
+    }
+    if (b->nwork_sc) {
+        a.work = b->d_work_sc;
+        stage_batch_kernel<T, D, DEPTH, 1, 128, 4, M32><<<b->nwork_sc, 128, 0, b->stream>>>(a);
+    }
+}
+
+template <typename T, int D, int DEPTH>
+static bool launch_batch_t(const chfpe_handle *b, const BatchStageArgs<T> &a) {
+    constexpr int M = member_count(D, DEPTH);
+    if (b->M32 == M) { launch_batch_m<T, D, DEPTH, M>(b, a); return true; }
+    if constexpr (sizeof(T) == 4 && D == 2 && DEPTH == 4) {
+        if (b->M32 == 6) { launch_batch_m<T, D, DEPTH, 6>(b, a); return true; }
+    }
+    if constexpr (sizeof(T) == 4 && D == 3 && DEPTH == 2) {
+        if (b->M32 == 4) { launch_batch_m<T, D, DEPTH, 4>(b, a); return true; }
+    }
+    return false;
+}
+
+// one RK4 stage over every instance of the batch: out = y + c M in  (arena base pointers)
+template <typename T>
+static chfpe_status batch_stage(chfpe_handle *b, const void *in, const void *y, void *out, double c) {
+    BatchStageArgs<T> a;
+    a.inst = (const InstGeo<T> *)b->d_geo;
+    a.work = nullptr;
+    a.in = (const char *)in;
+    a.y = (const char *)y;
+    a.out = (char *)out;
+    a.c = (T)c;
+    bool ok;
+#define CASE(D_, K_) \
+    case (D_ * 16 + K_): ok = launch_batch_t<T, D_, K_>(b, a); break;
+    switch (b->d * 16 + b->depth) {
+        CASE(1, 0) CASE(1, 1) CASE(1, 2) CASE(1, 3) CASE(1, 4) CASE(1, 5) CASE(1, 6) CASE(1, 7)
+        CASE(1, 8)
+        CASE(2, 0) CASE(2, 1) CASE(2, 2) CASE(2, 3) CASE(2, 4) CASE(2, 5)
+        CASE(3, 0) CASE(3, 1) CASE(3, 2) CASE(3, 3)
+        default: ok = false;
+    }
+#undef CASE
+    if (!ok) return fail(CHFPE_EINVAL, "unsupported (d, depth, bf16 tier) for batches");
+    CK(cudaGetLastError());
+    b->launches += (b->nwork_vec ? 1 : 0) + (b->nwork_sc ? 1 : 0);
+    return CHFPE_OK;
+}
+
+template <typename T>
+static chfpe_status batch_rk4(chfpe_handle *b, long nsteps) {
+    chfpe_status st;
+    const double dt = b->dt;
+    if (nsteps <= 0) return CHFPE_OK;
+    if (b->time_stages && (st = burst_event(b))) return st;
+    for (long k = 0; k < nsteps; ++k) {
+        if ((st = batch_stage<T>(b, b->cy, b->cy, b->ca, dt / 4.0))) return st;
+        if ((st = batch_stage<T>(b, b->ca, b->cy, b->cb, dt / 3.0))) return st;
+        if ((st = batch_stage<T>(b, b->cb, b->cy, b->ca, dt / 2.0))) return st;
+        if ((st = batch_stage<T>(b, b->ca, b->cy, b->cy, dt))) return st;
+    }
+    if (b->time_stages && (st = burst_event(b))) return st;
+    double bytes = 0.0;
+    for (chfpe_handle *c : b->inst) bytes += (double)c->state_bytes;
+    b->cell_updates += (double)nsteps * b->cells_total;
+    if (b->time_stages) {
+        b->stage_launches += 4 * nsteps * ((b->nwork_vec ? 1 : 0) + (b->nwork_sc ? 1 : 0));
+        b->stage_bytes += (double)nsteps * bytes * 11.0;
+    }
+    return CHFPE_OK;
+}
+
+template <typename T>
+static chfpe_status batch_setup_geo(chfpe_handle *b) {
+    const int n = (int)b->inst.size();
+    std::vector<InstGeo<T>> geo(n);
+    std::vector<int2> wv, ws;
+    for (int i = 0; i < n; ++i) {
+        geo[i].g = geo_of<T>(b->inst[i]);
+        geo[i].off = b->inst_off[i];
+        const chfpe_handle *c = b->inst[i];
+        const bool vec = c->n[2 * c->d - 1] % kVec == 0;
+        const int per_tile = 128 * (vec ? kVec : 1);
+        const int tiles = (c->P + per_tile - 1) / per_tile;
+        for (int t = 0; t < tiles; ++t) (vec ? wv : ws).push_back(make_int2(i, t));
+    }
+    chfpe_status st = CHFPE_OK;
+    b->d_geo = dalloc<InstGeo<T>>(n, &st);
+    if (!wv.empty()) b->d_work_vec = dalloc<int2>(wv.size(), &st);
+    if (!ws.empty()) b->d_work_sc = dalloc<int2>(ws.size(), &st);
+    if (st) return st;
+    b->nwork_vec = (int)wv.size();
+    b->nwork_sc = (int)ws.size();
+    CK(cudaMemcpyAsync(b->d_geo, geo.data(), n * sizeof(InstGeo<T>), cudaMemcpyHostToDevice, b->stream));
+    if (!wv.empty())
+        CK(cudaMemcpyAsync(b->d_work_vec, wv.data(), wv.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    if (!ws.empty())
+        CK(cudaMemcpyAsync(b->d_work_sc, ws.data(), ws.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_create_batch(int n, const chfpe_model *models, const chfpe_grid *grids,
+                                           const chfpe_options *opts, chfpe_handle **out) {
+    if (!out || !models || !grids || !opts) return fail(CHFPE_EINVAL, "null argument");
+    *out = nullptr;
+    if (n < 1) return fail(CHFPE_EINVAL, "n must be >= 1");
+    for (int i = 0; i < n; ++i) {
+        chfpe_status st = validate(&models[i], &grids[i], opts);
+        if (st) return fail(st, "instance " + std::to_string(i) + ": " + g_err);
+        if (models[i].nmodes != models[0].nmodes)
+            return fail(CHFPE_EINVAL, "all instances of a batch must have the same number of modes");
+    }
+    // one RK4 step of the batch = nsub substeps of dt / nsub, nsub the smallest power of two that
+    // keeps every instance inside the stability bound
+    int nsub = 1;
+    for (int i = 0; i < n; ++i) {
+        const double rho = bound_for(&models[i], &grids[i], opts->depth);
+        while (opts->dt / nsub * rho > 2.6 && nsub < (1 << 12)) nsub *= 2;
+    }
+    chfpe_handle *b = new chfpe_handle();
+    b->model = models[0];
+    b->grid = grids[0];
+    b->opts = *opts;
+    b->d = models[0].nmodes;
+    b->depth = opts->depth;
+    b->M = member_count(b->d, b->depth);
+    b->prec = opts->precision;
+    b->esize = b->prec == 64 ? 8 : 4;
+    b->nsub = nsub;
+    b->dt = opts->dt / nsub;
+    if (opts->stream) {
+        b->stream = (cudaStream_t)opts->stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete b; return fail(CHFPE_ECUDA, cudaGetErrorString(e)); }
+        b->own_stream = true;
+    }
+    chfpe_options io = *opts;
+    io.dt = b->dt;
+    io.max_batch = 0;
+    io.stream = b->stream;
+    chfpe_status st = CHFPE_OK;
+    long long total = 0;
+    for (int i = 0; i < n && !st; ++i) {
+        chfpe_handle *c = nullptr;
+        st = create_impl(&models[i], &grids[i], &io, true, &c);
+        if (st) { st = fail(st, "instance " + std::to_string(i) + ": " + g_err); break; }
+        b->inst.push_back(c);
+        b->inst_off.push_back(total);
+        total += (c->state_bytes + 255) / 256 * 256;
+        b->cells_total += (double)c->state;
+    }
+    b->M32 = b->inst.empty() ? b->M : b->inst[0]->M32;
+    b->partial_cap = 4096;
+    if (!st) b->partial = dalloc<double>(b->partial_cap, &st);
+    if (!st) b->counter = dalloc<int>(1, &st);
+    void **arenas[] = {&b->cy, &b->ca, &b->cb, &b->eq};
+    for (void **p : arenas) if (!st) *p = (void *)dalloc<char>((size_t)total, &st);
+    if (st) { chfpe_destroy(b); return st; }
+    for (int i = 0; i < n; ++i) {
+        chfpe_handle *c = b->inst[i];
+        c->cy = (char *)b->cy + b->inst_off[i];
+        c->ca = (char *)b->ca + b->inst_off[i];
+        c->cb = (char *)b->cb + b->inst_off[i];
+        c->eq = (char *)b->eq + b->inst_off[i];
+    }
+    st = b->prec == 64 ? batch_setup_geo<double>(b) : batch_setup_geo<float>(b);
+    if (st) { chfpe_destroy(b); return st; }
+    *out = b;
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_batch_instance(chfpe_handle *b, int i, chfpe_handle **inst) {
+    if (!b || !inst) return fail(CHFPE_EINVAL, "null argument");
+    if (i < 0 || i >= (int)b->inst.size()) return fail(CHFPE_EINVAL, "instance index out of range");
+    *inst = b->inst[i];
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_batch_equilibrate(chfpe_handle *b, long max_steps, double tol,
+                                                long check_every, double *residuals) {
+    if (!b || b->inst.empty()) return fail(CHFPE_EINVAL, "not a batch handle");
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        double r = 0.0;
+        chfpe_status st = chfpe_equilibrate(b->inst[i], max_steps * b->nsub, tol,
+                                            check_every * b->nsub, nullptr, &r);
+        if (st) return fail(st, "instance " + std::to_string(i) + ": " + g_err);
+        if (residuals) residuals[i] = r;
+    }
+    return CHFPE_OK;
+}
+
+// R1 of every instance: R[i * nt + k], one fused launch per RK4 stage for the whole batch
+extern "C" chfpe_status chfpe_batch_response1(chfpe_handle *b, const chfpe_optical *A,
+                                              const chfpe_optical *C, int nt, int stride, double *R) {
+    if (!b || b->inst.empty() || !A || !C || !R) return fail(CHFPE_EINVAL, "null argument or not a batch");
+    if (nt < 1 || stride < 0) return fail(CHFPE_EINVAL, "nt >= 1, stride >= 0");
+    const int n = (int)b->inst.size();
+    chfpe_status st;
+    for (int i = 0; i < n; ++i)
+        if (!b->inst[i]->have_eq) return fail(CHFPE_ESTATE, "instance " + std::to_string(i) + " has no equilibrium");
+    if ((st = ensure_dR(b, (size_t)n * nt))) return st;
+    for (int i = 0; i < n; ++i) {
+        chfpe_handle *c = b->inst[i];
+        if ((st = set_observable(c, C))) return st;
+        if ((st = insert(c, A, c->eq, 0, c->cy, 1))) return st;
+    }
+    auto observe_all = [&](int k, const int *counter) -> chfpe_status {
+        for (int i = 0; i < n; ++i) {
+            chfpe_status s2 = observe(b->inst[i], b->inst[i]->cy, 1, b->dR + (size_t)i * nt + k, 1, counter);
+            if (s2) return s2;
+        }
+        return CHFPE_OK;
+    };
+    const long steps = (long)stride * b->nsub;
+    auto advance = [&]() -> chfpe_status {
+        return b->prec == 64 ? batch_rk4<double>(b, steps) : batch_rk4<float>(b, steps);
+    };
+    if ((st = observe_all(0, nullptr))) return st;
+    const bool graphs = b->use_graphs != 0 && nt > 2 && steps > 0 && !b->time_stages &&
+                        b->cells_total * 4.0 * steps < 2e9;
+    if (!graphs) {
+        for (int k = 1; k < nt; ++k) {
+            if ((st = advance())) return st;
+            if ((st = observe_all(k, nullptr))) return st;
+        }
+    } else {
+        const int one = 1;
+        CK(cudaMemcpyAsync(b->counter, &one, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        // instances share the batch stream, so their observation kernels are captured too
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        st = advance();
+        if (!st) st = observe_all(0, b->counter);
+        if (!st) counter_add_kernel<<<1, 1, 0, b->stream>>>(b->counter, 1);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (st) { if (graph) cudaGraphDestroy(graph); return st; }
+        if (e != cudaSuccess) return fail(CHFPE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(CHFPE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        for (int k = 1; k < nt && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, b->stream);
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return fail(CHFPE_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+        b->cell_updates += (double)(nt - 2) * steps * b->cells_total;
+    }
+    return finish_response(b, R, (size_t)n * nt);
 }

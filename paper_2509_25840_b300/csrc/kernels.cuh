@@ -23,6 +23,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cuda_bf16.h>
 
 namespace chfpe {
 
@@ -84,21 +85,18 @@ struct MemberTable {
 };
 
 // ------------------------------------------------------------------------------------------
-// kernel arguments (passed by value)
+// per-instance geometry and coefficients; stage arguments
 // ------------------------------------------------------------------------------------------
 
+typedef __nv_bfloat16 bf16;
+
 template <typename T>
-struct StageArgs {
-    const T *in;          // stencil input, batch of states
-    const T *y;           // base state (same batch layout) or nullptr: out = c * M in
-    T *out;
-    long long state;      // values per state (M * P)
+struct Geo {
     int P;                // points per member
     int n[6];             // axis sizes: q_1..q_d, p_1..p_d
     int st[6];            // axis strides inside one member
     int Pp;               // points of the p-subgrid (q index = x / Pp)
     int NQ;               // points of the q-subgrid
-    T c;                  // stage coefficient
     const T *F;           // [D][NQ]  dU/dq_s / (60 h_ps)
     T qlo[3], qh[3], plo[3], ph[3];
     T vq[3];              // 1 / (m_s 60 h_qs)
@@ -107,6 +105,18 @@ struct StageArgs {
     T VLL[3], VSL[3];
     T gam[3];
     T link[3][kMaxDepth + 2];   // sqrt(k c_s)
+};
+
+// Storage of one state: members [0, M32) as T, members [M32, M) as bf16 (deep tiers, only with
+// T = float); M32 = M is the plain layout.  A batch of states is contiguous, state_bytes apart.
+template <typename T>
+struct StageArgs {
+    const char *in;       // stencil input, batch of states
+    const char *y;        // base states (same layout) or nullptr: out = c * M in
+    char *out;
+    long long state_bytes;
+    T c;                  // stage coefficient
+    Geo<T> g;
 };
 
 template <typename T>
@@ -122,103 +132,19 @@ __device__ __forceinline__ T stencil7(const T *__restrict__ f, int x, int i, int
 }
 
 // ------------------------------------------------------------------------------------------
-// fused RHS + RK4 stage
-// ------------------------------------------------------------------------------------------
-
-template <typename T, int D, int DEPTH>
-__global__ void __launch_bounds__(256) stage_kernel(const StageArgs<T> a) {
-    constexpr MemberTable<D, DEPTH> tab{};
-    constexpr int M = MemberTable<D, DEPTH>::M;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= a.P) return;
-    const long long boff = (long long)blockIdx.y * a.state;
-    const T *__restrict__ in = a.in + boff;
-
-    int idx[2 * D];
-    {
-        int r = x;
-#pragma unroll
-        for (int ax = 2 * D - 1; ax >= 0; --ax) {
-            idx[ax] = r % a.n[ax];
-            r /= a.n[ax];
-        }
-    }
-    const int qlin = x / a.Pp;
-
-    T Fs[D], vq[D], VpD[D], VpK[D];
-#pragma unroll
-    for (int s = 0; s < D; ++s) {
-        const T q = a.qlo[s] + T(idx[s]) * a.qh[s];
-        const T p = a.plo[s] + T(idx[D + s]) * a.ph[s];
-        const T Vp = a.VLL[s] + a.VSL[s] * q;
-        Fs[s] = __ldg(a.F + s * a.NQ + qlin);
-        vq[s] = p * a.vq[s];
-        VpD[s] = Vp * a.inv60hp[s];
-        VpK[s] = Vp * a.kappa[s] * p;
-    }
-
-    T acc[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) acc[m] = T(0);
-
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        const T *__restrict__ g = in + (long long)m * a.P;
-        const T v = __ldg(g + x);
-        T dp[D];
-        T k = T(0);
-        T gm = T(0);
-#pragma unroll
-        for (int s = 0; s < D; ++s) {
-            const T dq = stencil7(g, x, idx[s], a.n[s], a.st[s]);
-            dp[s] = stencil7(g, x, idx[D + s], a.n[D + s], a.st[D + s]);
-            k += Fs[s] * dp[s] - vq[s] * dq;
-            gm += T(tab.n[m][s]) * a.gam[s];
-        }
-        acc[m] += k - gm * v;
-#pragma unroll
-        for (int s = 0; s < D; ++s) {
-            if (tab.dn[m][s] >= 0) {
-                const T w = a.link[s][tab.n[m][s]];
-                acc[tab.dn[m][s]] += w * (VpD[s] * dp[s] - VpK[s] * v);
-            }
-            if (tab.up[m][s] >= 0) {
-                const T w = a.link[s][tab.n[m][s] + 1];
-                acc[tab.up[m][s]] += w * (VpD[s] * dp[s] + VpK[s] * v);
-            }
-        }
-    }
-
-    T *__restrict__ out = a.out + boff;
-    if (a.y) {
-        const T *__restrict__ y = a.y + boff;
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const long long o = (long long)m * a.P + x;
-            out[o] = y[o] + a.c * acc[m];
-        }
-    } else {
-#pragma unroll
-        for (int m = 0; m < M; ++m) out[(long long)m * a.P + x] = a.c * acc[m];
-    }
-}
-
-// ------------------------------------------------------------------------------------------
-// fused RHS + RK4 stage, vectorised along the fastest axis p_d
-//
-// Thread t owns the V consecutive points x0 = V t .. x0 + V - 1 of one p_d row (n_pd % V == 0,
-// so a row never straddles two vectors and every vector access is aligned to V elements).  A
-// neighbour along any other axis is one V-wide load for all V points; the p_d stencil reads a
-// window of (2 NS + 1) vectors, NS = ceil(3 / V).  Per member: 1 + 6 (2d - 1) + 2 NS vector loads
-// for V cells instead of 1 + 12 d scalar loads per cell.
+// vector loads / stores of V consecutive values, stored as T or as bf16
 // ------------------------------------------------------------------------------------------
 
 template <typename T, int V> struct VecOf;
 template <> struct VecOf<float, 4> { typedef float4 type; };
 template <> struct VecOf<float, 2> { typedef float2 type; };
+template <> struct VecOf<float, 1> { typedef float type; };
 template <> struct VecOf<double, 2> { typedef double2 type; };
 template <> struct VecOf<double, 1> { typedef double type; };
-template <> struct VecOf<float, 1> { typedef float type; };
+template <int V> struct BfVecOf;
+template <> struct BfVecOf<1> { typedef unsigned short type; };
+template <> struct BfVecOf<2> { typedef unsigned int type; };
+template <> struct BfVecOf<4> { typedef uint2 type; };
 
 template <typename T, int V>
 __device__ __forceinline__ void vload(const T *__restrict__ p, bool ok, T (&v)[V]) {
@@ -228,6 +154,20 @@ __device__ __forceinline__ void vload(const T *__restrict__ p, bool ok, T (&v)[V
         const T *e = reinterpret_cast<const T *>(&u);
 #pragma unroll
         for (int j = 0; j < V; ++j) v[j] = e[j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] = T(0);
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void vload(const bf16 *__restrict__ p, bool ok, T (&v)[V]) {
+    typedef typename BfVecOf<V>::type VT;
+    if (ok) {
+        const VT u = __ldg(reinterpret_cast<const VT *>(p));
+        const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] = (T)__bfloat162float(e[j]);
     } else {
 #pragma unroll
         for (int j = 0; j < V; ++j) v[j] = T(0);
@@ -245,6 +185,15 @@ __device__ __forceinline__ void vload_rw(const T *p, T (&v)[V]) {
 }
 
 template <typename T, int V>
+__device__ __forceinline__ void vload_rw(const bf16 *p, T (&v)[V]) {
+    typedef typename BfVecOf<V>::type VT;
+    const VT u = *reinterpret_cast<const VT *>(p);
+    const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+    for (int j = 0; j < V; ++j) v[j] = (T)__bfloat162float(e[j]);
+}
+
+template <typename T, int V>
 __device__ __forceinline__ void vstore(T *p, const T (&v)[V]) {
     typedef typename VecOf<T, V>::type VT;
     VT u;
@@ -254,9 +203,19 @@ __device__ __forceinline__ void vstore(T *p, const T (&v)[V]) {
     *reinterpret_cast<VT *>(p) = u;
 }
 
-// (45 (f+1 - f-1) - 9 (f+2 - f-2) + (f+3 - f-3)) along a non-fastest axis, V points at once
 template <typename T, int V>
-__device__ __forceinline__ void vstencil(const T *__restrict__ f, int x0, int i, int N, int st,
+__device__ __forceinline__ void vstore(bf16 *p, const T (&v)[V]) {
+    typedef typename BfVecOf<V>::type VT;
+    VT u;
+    bf16 *e = reinterpret_cast<bf16 *>(&u);
+#pragma unroll
+    for (int j = 0; j < V; ++j) e[j] = __float2bfloat16_rn((float)v[j]);   // round to nearest even
+    *reinterpret_cast<VT *>(p) = u;
+}
+
+// (45 (f+1 - f-1) - 9 (f+2 - f-2) + (f+3 - f-3)) along a non-fastest axis, V points at once
+template <typename S, typename T, int V>
+__device__ __forceinline__ void vstencil(const S *__restrict__ f, int x0, int i, int N, int st,
                                          T (&out)[V]) {
     T p1[V], m1[V], p2[V], m2[V], p3[V], m3[V];
     vload<T, V>(f + x0 + st, i + 1 < N, p1);
@@ -270,17 +229,77 @@ __device__ __forceinline__ void vstencil(const T *__restrict__ f, int x0, int i,
         out[j] = T(45) * (p1[j] - m1[j]) - T(9) * (p2[j] - m2[j]) + (p3[j] - m3[j]);
 }
 
-template <typename T, int D, int DEPTH, int V, int NT, int MINB = 1>
-__global__ void __launch_bounds__(NT, MINB) stage_vec_kernel(const StageArgs<T> a) {
+// member m of a state at `base`: T storage below M32, bf16 from M32 on
+template <typename T, int M32>
+__device__ __forceinline__ const T *member_t(const char *base, int m, int P) {
+    return reinterpret_cast<const T *>(base) + (long long)m * P;
+}
+template <typename T, int M32>
+__device__ __forceinline__ const bf16 *member_h(const char *base, int m, int P) {
+    return reinterpret_cast<const bf16 *>(reinterpret_cast<const T *>(base) + (long long)M32 * P) +
+           (long long)(m - M32) * P;
+}
+
+// one member at V points: its own Liouvillian terms k = sum_s [F_s D_ps g - v_s D_qs g] (the
+// q-derivatives are consumed at once), its p-derivatives dp_s (kept for the hierarchy links) and
+// its values; the p_d derivative comes from a window of (2 NS + 1) vectors
+template <typename S, typename T, int D, int V>
+__device__ __forceinline__ void member_terms(const S *__restrict__ g, const Geo<T> &a, int x0,
+                                             const int (&idx)[2 * D], const T (&Fs)[D],
+                                             const T (&vq)[D][V], T (&k)[V], T (&dp)[D][V],
+                                             T (&v)[V]) {
+    constexpr int NS = (3 + V - 1) / V;          // side vectors of the p_d window
+    constexpr int WN = (2 * NS + 1) * V;
+    constexpr int L = 2 * D - 1;
+    const int iL = idx[L], NL = a.n[L];
+    T w[WN];
+#pragma unroll
+    for (int b = 0; b < 2 * NS + 1; ++b) {
+        const int off = (b - NS) * V;
+        T tmp[V];
+        vload<T, V>(g + x0 + off, iL + off >= 0 && iL + off < NL, tmp);
+#pragma unroll
+        for (int j = 0; j < V; ++j) w[b * V + j] = tmp[j];
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) k[j] = T(0);
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+        T dq[V];
+        vstencil<S, T, V>(g, x0, idx[s], a.n[s], a.st[s], dq);
+        if (s < D - 1) {
+            vstencil<S, T, V>(g, x0, idx[D + s], a.n[D + s], a.st[D + s], dp[s]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int c = NS * V + j;
+                dp[s][j] = T(45) * (w[c + 1] - w[c - 1]) - T(9) * (w[c + 2] - w[c - 2]) +
+                           (w[c + 3] - w[c - 3]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j) k[j] += Fs[s] * dp[s][j] - vq[s][j] * dq[j];
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) v[j] = w[NS * V + j];
+}
+
+// ------------------------------------------------------------------------------------------
+// fused RHS + RK4 stage for V consecutive p_d points of one state
+//
+// The thread owns the V points x0 .. x0 + V - 1 of one p_d row (n_pd % V == 0, so a row never
+// straddles two vectors and every vector access is aligned to V elements) for every member.
+// Members are unrolled at compile time: each member's p-derivatives are formed once and pushed
+// into register accumulators of the member itself and of its two neighbours per mode.  A
+// neighbour along any other axis is one V-wide load for all V points; the p_d stencil reads a
+// window of (2 NS + 1) vectors, NS = ceil(3 / V).
+// ------------------------------------------------------------------------------------------
+
+template <typename T, int D, int DEPTH, int V, int M32>
+__device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, const char *y,
+                                             char *out, T c, int x0) {
     constexpr MemberTable<D, DEPTH> tab{};
     constexpr int M = MemberTable<D, DEPTH>::M;
-    constexpr int NS = (3 + V - 1) / V;          // side vectors of the p_d window
-    constexpr int WN = (2 * NS + 1) * V;         // window length
-    constexpr int L = 2 * D - 1;                 // fastest axis
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    if (x0 >= a.P) return;
-    const long long boff = (long long)blockIdx.y * a.state;
-    const T *__restrict__ in = a.in + boff;
 
     int idx[2 * D];
     {
@@ -316,83 +335,94 @@ __global__ void __launch_bounds__(NT, MINB) stage_vec_kernel(const StageArgs<T> 
 #pragma unroll
         for (int j = 0; j < V; ++j) acc[m][j] = T(0);
 
-    const int iL = idx[L], NL = a.n[L];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-        const T *__restrict__ g = in + (long long)m * a.P;
-        // p_d window: f[x0 - NS V .. x0 + (NS + 1) V - 1]
-        T w[WN];
-#pragma unroll
-        for (int b = 0; b < 2 * NS + 1; ++b) {
-            const int off = (b - NS) * V;
-            T tmp[V];
-            vload<T, V>(g + x0 + off, iL + off >= 0 && iL + off < NL, tmp);
-#pragma unroll
-            for (int j = 0; j < V; ++j) w[b * V + j] = tmp[j];
-        }
-        T dp[D][V];
-        T k[V];
-#pragma unroll
-        for (int j = 0; j < V; ++j) k[j] = T(0);
-#pragma unroll
-        for (int s = 0; s < D; ++s) {
-            T dq[V];
-            vstencil<T, V>(g, x0, idx[s], a.n[s], a.st[s], dq);
-            if (s < D - 1) {
-                vstencil<T, V>(g, x0, idx[D + s], a.n[D + s], a.st[D + s], dp[s]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < V; ++j) {
-                    const int c = NS * V + j;
-                    dp[s][j] = T(45) * (w[c + 1] - w[c - 1]) - T(9) * (w[c + 2] - w[c - 2]) +
-                               (w[c + 3] - w[c - 3]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < V; ++j) k[j] += Fs[s] * dp[s][j] - vq[s][j] * dq[j];
-        }
+        T k[V], dp[D][V], v[V];
+        if (m < M32)
+            member_terms<T, T, D, V>(member_t<T, M32>(in, m, a.P), a, x0, idx, Fs, vq, k, dp, v);
+        else
+            member_terms<bf16, T, D, V>(member_h<T, M32>(in, m, a.P), a, x0, idx, Fs, vq, k, dp, v);
         T gm = T(0);
 #pragma unroll
         for (int s = 0; s < D; ++s) gm += T(tab.n[m][s]) * a.gam[s];
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-            const T v = w[NS * V + j];
-            acc[m][j] += k[j] - gm * v;
+            acc[m][j] += k[j] - gm * v[j];
 #pragma unroll
             for (int s = 0; s < D; ++s) {
                 if (tab.dn[m][s] >= 0) {
                     const T wl = a.link[s][tab.n[m][s]];
-                    acc[tab.dn[m][s]][j] += wl * (VpD[s] * dp[s][j] - VpK[s][j] * v);
+                    acc[tab.dn[m][s]][j] += wl * (VpD[s] * dp[s][j] - VpK[s][j] * v[j]);
                 }
                 if (tab.up[m][s] >= 0) {
                     const T wl = a.link[s][tab.n[m][s] + 1];
-                    acc[tab.up[m][s]][j] += wl * (VpD[s] * dp[s][j] + VpK[s][j] * v);
+                    acc[tab.up[m][s]][j] += wl * (VpD[s] * dp[s][j] + VpK[s][j] * v[j]);
                 }
             }
         }
     }
 
-    T *out = a.out + boff;
-    if (a.y) {
-        const T *y = a.y + boff;
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const long long o = (long long)m * a.P + x0;
-            T yv[V], r[V];
-            vload_rw<T, V>(y + o, yv);
+    for (int m = 0; m < M; ++m) {
+        T r[V];
+        if (y) {
+            T yv[V];
+            if (m < M32)
+                vload_rw<T, V>(member_t<T, M32>(y, m, a.P) + x0, yv);
+            else
+                vload_rw<T, V>(member_h<T, M32>(y, m, a.P) + x0, yv);
 #pragma unroll
-            for (int j = 0; j < V; ++j) r[j] = yv[j] + a.c * acc[m][j];
-            vstore<T, V>(out + o, r);
+            for (int j = 0; j < V; ++j) r[j] = yv[j] + c * acc[m][j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) r[j] = c * acc[m][j];
         }
-    } else {
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            T r[V];
-#pragma unroll
-            for (int j = 0; j < V; ++j) r[j] = a.c * acc[m][j];
-            vstore<T, V>(out + (long long)m * a.P + x0, r);
-        }
+        if (m < M32)
+            vstore<T, V>(const_cast<T *>(member_t<T, M32>(out, m, a.P)) + x0, r);
+        else
+            vstore<T, V>(const_cast<bf16 *>(member_h<T, M32>(out, m, a.P)) + x0, r);
     }
+}
+
+template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32>
+__global__ void __launch_bounds__(NT, MINB) stage_vec_kernel(const StageArgs<T> a) {
+    const int x0 = (blockIdx.x * NT + threadIdx.x) * V;
+    if (x0 >= a.g.P) return;
+    const long long boff = (long long)blockIdx.y * a.state_bytes;
+    stage_points<T, D, DEPTH, V, M32>(a.g, a.in + boff, a.y ? a.y + boff : nullptr, a.out + boff,
+                                      a.c, x0);
+}
+
+// ------------------------------------------------------------------------------------------
+// the same stage over many instances of different grids in one launch: a work list of
+// (instance, tile) items, one tile of NT * V points per block
+// ------------------------------------------------------------------------------------------
+
+template <typename T>
+struct InstGeo {
+    Geo<T> g;
+    long long off;        // byte offset of the instance's state inside each batch arena
+};
+
+template <typename T>
+struct BatchStageArgs {
+    const InstGeo<T> *inst;
+    const int2 *work;     // (instance, tile)
+    const char *in;
+    const char *y;
+    char *out;
+    T c;
+};
+
+template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32>
+__global__ void __launch_bounds__(NT, MINB) stage_batch_kernel(const BatchStageArgs<T> b) {
+    const int2 item = b.work[blockIdx.x];
+    const InstGeo<T> &ig = b.inst[item.x];
+    const int x0 = (item.y * NT + threadIdx.x) * V;
+    if (x0 >= ig.g.P) return;
+    const long long off = ig.off;
+    stage_points<T, D, DEPTH, V, M32>(ig.g, b.in + off, b.y ? b.y + off : nullptr, b.out + off,
+                                      b.c, x0);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -401,10 +431,10 @@ __global__ void __launch_bounds__(NT, MINB) stage_vec_kernel(const StageArgs<T> 
 
 template <typename T>
 struct InsertArgs {
-    const T *in;
-    T *out;
-    long long in_state, out_state;   // batch strides (in_state may be 0: one input, many outputs)
-    int P, M, d;
+    const char *in;
+    char *out;
+    long long in_state, out_state;   // batch strides in bytes (in_state may be 0: one input)
+    int P, M, M32, d;                // members >= M32 are stored as bf16
     int n[6], st[6];
     T qlo[3], qh[3], plo[3], ph[3];
     T lin[3];
@@ -412,12 +442,41 @@ struct InsertArgs {
     T inv60hp[3], kappa[3];
 };
 
+template <typename S, typename T>
+__device__ __forceinline__ T ldv(const S *p) { return (T)__ldg(p); }
+template <>
+__device__ __forceinline__ float ldv<bf16, float>(const bf16 *p) { return __bfloat162float(__ldg(p)); }
+
+template <typename S, typename T>
+__device__ __forceinline__ T stencil7s(const S *__restrict__ f, int x, int i, int N, int st) {
+    T p1 = (i + 1 < N) ? ldv<S, T>(f + x + st) : T(0);
+    T m1 = (i >= 1) ? ldv<S, T>(f + x - st) : T(0);
+    T p2 = (i + 2 < N) ? ldv<S, T>(f + x + 2 * st) : T(0);
+    T m2 = (i >= 2) ? ldv<S, T>(f + x - 2 * st) : T(0);
+    T p3 = (i + 3 < N) ? ldv<S, T>(f + x + 3 * st) : T(0);
+    T m3 = (i >= 3) ? ldv<S, T>(f + x - 3 * st) : T(0);
+    return T(45) * (p1 - m1) - T(9) * (p2 - m2) + (p3 - m3);
+}
+
+template <typename S, typename T>
+__device__ __forceinline__ void insert_member(const InsertArgs<T> &a, const S *__restrict__ g,
+                                              S *o, int x, const int *idx, const T *G,
+                                              const T *Kp) {
+    const T v = ldv<S, T>(g + x);
+    T acc = T(0);
+    for (int s = 0; s < a.d; ++s) {
+        const T dp = stencil7s<S, T>(g, x, idx[a.d + s], a.n[a.d + s], a.st[a.d + s]);
+        acc += G[s] * dp - Kp[s] * v;
+    }
+    o[x] = (S)acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) insert_kernel(const InsertArgs<T> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= a.P) return;
-    const T *__restrict__ in = a.in + (long long)blockIdx.y * a.in_state;
-    T *__restrict__ out = a.out + (long long)blockIdx.y * a.out_state;
+    const char *in = a.in + (long long)blockIdx.y * a.in_state;
+    char *out = a.out + (long long)blockIdx.y * a.out_state;
     const int d = a.d;
     int idx[6];
     int r = x;
@@ -434,15 +493,46 @@ __global__ void __launch_bounds__(256) insert_kernel(const InsertArgs<T> a) {
         Kp[s] = gs * a.kappa[s] * p;
     }
     for (int m = 0; m < a.M; ++m) {
-        const T *__restrict__ g = in + (long long)m * a.P;
-        const T v = __ldg(g + x);
-        T acc = T(0);
-        for (int s = 0; s < d; ++s) {
-            const T dp = stencil7(g, x, idx[d + s], a.n[d + s], a.st[d + s]);
-            acc += G[s] * dp - Kp[s] * v;
+        if (m < a.M32) {
+            const T *g = reinterpret_cast<const T *>(in) + (long long)m * a.P;
+            T *o = reinterpret_cast<T *>(out) + (long long)m * a.P;
+            insert_member<T, T>(a, g, o, x, idx, G, Kp);
+        } else {
+            const long long hoff = (long long)a.M32 * a.P * sizeof(T);
+            const bf16 *g = reinterpret_cast<const bf16 *>(in + hoff) + (long long)(m - a.M32) * a.P;
+            bf16 *o = reinterpret_cast<bf16 *>(out + hoff) + (long long)(m - a.M32) * a.P;
+            const T v = __bfloat162float(__ldg(g + x));
+            T acc = T(0);
+            for (int s = 0; s < d; ++s) {
+                const T dp = stencil7s<bf16, T>(g, x, idx[d + s], a.n[d + s], a.st[d + s]);
+                acc += G[s] * dp - Kp[s] * v;
+            }
+            o[x] = __float2bfloat16_rn((float)acc);
         }
-        out[(long long)m * a.P + x] = acc;
     }
+}
+
+// double <-> mixed storage (members [0, M32) as T, the rest as bf16), one state
+template <typename T>
+__global__ void to_mixed_kernel(const double *in, char *out, long long n_t, long long n_total) {
+    T *o = reinterpret_cast<T *>(out);
+    bf16 *oh = reinterpret_cast<bf16 *>(o + n_t);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_total;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < n_t)
+            o[i] = (T)in[i];
+        else
+            oh[i - n_t] = __double2bfloat16(in[i]);
+    }
+}
+
+template <typename T>
+__global__ void from_mixed_kernel(const char *in, double *out, long long n_t, long long n_total) {
+    const T *g = reinterpret_cast<const T *>(in);
+    const bf16 *gh = reinterpret_cast<const bf16 *>(g + n_t);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_total;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (i < n_t) ? (double)g[i] : (double)__bfloat162float(gh[i - n_t]);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -489,8 +579,8 @@ __device__ __forceinline__ double block_max(double v) {
 }
 
 struct ObserveArgs {
-    const void *in;          // batch of states (T), member 0 is read
-    long long state;
+    const void *in;          // batch of states, member 0 (stored as T) is read
+    long long state_bytes;
     int P, Pp, d;
     int np[3];               // p-axis sizes
     const double *CWq;       // [NQ]: C(q) exp(-U(q)/2kT)
@@ -503,7 +593,8 @@ struct ObserveArgs {
 // block b of state j sums points b, b + nblk*NT, ... (grid-stride) into partial[j][b]
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) observe_partial_kernel(const ObserveArgs a) {
-    const T *__restrict__ g = (const T *)a.in + (long long)blockIdx.y * a.state;
+    const T *__restrict__ g =
+        reinterpret_cast<const T *>((const char *)a.in + (long long)blockIdx.y * a.state_bytes);
     double sum = 0.0;
     for (int x = blockIdx.x * NT + threadIdx.x; x < a.P; x += a.nblk * NT) {
         const int qlin = x / a.Pp;
@@ -530,6 +621,21 @@ static __global__ void observe_finish_kernel(const double *partial, int nblk, in
     s = warp_sum(s);
     if (threadIdx.x == 0) out[(long long)j * out_stride] = scale * s;
 }
+
+// the same, written to out[j * out_stride + *counter]: the output slot comes from a device
+// counter so that a captured graph of one sampling interval can be replayed unchanged
+static __global__ void observe_finish_counter_kernel(const double *partial, int nblk, int batch,
+                                                     double scale, double *out,
+                                                     long long out_stride, const int *counter) {
+    const int j = blockIdx.x;
+    if (j >= batch) return;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += partial[(long long)j * nblk + b];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) out[(long long)j * out_stride + *counter] = scale * s;
+}
+
+static __global__ void counter_add_kernel(int *counter, int inc) { *counter += inc; }
 
 // Boltzmann: g0[x] = exp(-(U(q) + sum p^2/2m) / 2kT); partial sums of g0^2
 template <int NT>
@@ -582,7 +688,7 @@ __global__ void __launch_bounds__(NT) absmax_partial_kernel(const T *x, long lon
 }
 
 template <typename S, typename D_>
-__global__ void convert_kernel(const S *in, D_ *out, long long n) {
+__global__ void convert_kernel(const S *in, D_ *out, long long n) {   // plain element conversion
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         out[i] = (D_)in[i];

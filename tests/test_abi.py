@@ -42,7 +42,8 @@ def test_create_rejects_invalid_arguments_on_cpu():
         dict(depth=9),                 # beyond the compiled range for one mode
         dict(dt=1.0),                  # above the RK4 stability bound
         dict(precision=16),
-        dict(max_batch=0),
+        dict(max_batch=-1),
+        dict(bf16_tier=2),             # not a compiled (modes, depth, tier) combination
     ]
     for kw in bad:
         args = dict(depth=wl.depth, dt=wl.dt, precision=32, max_batch=1)
