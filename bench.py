@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--eq-steps", type=int, default=200, help="FP64 equilibration steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="two_mode_32",
+                    choices=["two_mode_32", "one_mode_64", "three_mode_20", "sweep"],
+                    help="two_mode_32 is the benchmark; the others are secondary measurements")
+    ap.add_argument("--instances", type=int, default=64, help="sweep: instances in the batch")
     return ap.parse_args()
 
 
@@ -311,12 +315,107 @@ def run_ours(args, rank, world, local, pg):
     h.close()
 
 
+# ------------------------------------------------------------------------------------------
+# secondary workloads (one GPU): the one-mode R1, the three-mode 20^6 R2 on a reduced t-grid,
+# and the batched parameter sweep with bf16 deep tiers
+# ------------------------------------------------------------------------------------------
+
+def run_extra(args, local):
+    import numpy as np
+    import torch
+    from paper_2509_25840_b300 import chfpe
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    peak, peak_kind = peaks()
+    t_eq = time.perf_counter()
+    if args.workload == "one_mode_64":
+        wl = inputs.one_mode_64()
+        prec, dtype = 64, "f64"
+        h = chfpe.Handle(wl.model, wl.grid, depth=wl.depth, dt=wl.dt, precision=prec,
+                         stream=stream.cuda_stream)
+        eq = h.equilibrate(args.eq_steps, 1e-12, max(1, args.eq_steps))
+        units = wl.cells * (wl.nt1 - 1) * wl.stride
+        step = lambda: h.response1(wl.A, wl.C, wl.nt1, wl.stride)
+        desc = ("one_mode_64: 1 harmonic mode, 64x64 on [-6,6]^2, zeta=0.2, gamma=1, LL, depth 5, "
+                "dt=0.005, R1 sampled every step over 2000 steps (CUDA-graph sampling intervals)")
+        unit_name = "R1 responses"
+    elif args.workload == "three_mode_20":
+        nt = args.nt if args.nt != 64 else 8
+        wl = inputs.three_mode_20(nt=nt)
+        prec, dtype = 32, "f32"
+        h = chfpe.Handle(wl.model, wl.grid, depth=wl.depth, dt=wl.dt, precision=prec,
+                         max_batch=nt, stream=stream.cuda_stream)
+        eq = h.equilibrate(min(args.eq_steps, 20), 1e-10, max(1, min(args.eq_steps, 20)))
+        units = wl.cells * wl.r2_state_steps()
+        step = lambda: h.response2(wl.A, wl.B, wl.C, nt, nt, wl.stride)
+        full = inputs.three_mode_20()
+        desc = ("three_mode_20: 3 water-like modes (omega 0.5/1.0/1.6), 20^6 grid, depth 2 (10 members),"
+                " dt=0.002, TRT R2 on %dx%d at dtau=0.1 (the 128x128 spectrum needs %d state-steps)"
+                % (nt, nt, full.r2_state_steps()))
+        unit_name = "R2 spectra (reduced t-grid)"
+    else:
+        n = args.instances
+        wls = [inputs.sweep_instance(s) for s in range(n)]
+        prec, dtype = 32, "f32+bf16(tiers 3-4)"
+        h = chfpe.Batch([w.model for w in wls], [w.grid for w in wls], depth=4, dt=0.005,
+                        precision=32, stream=stream.cuda_stream, bf16_tier=3)
+        res = h.equilibrate_all(min(args.eq_steps, 50), 1e-10, max(1, min(args.eq_steps, 50)))
+        eq = (min(args.eq_steps, 50), float(np.max(res)))
+        nt, stride = 201, 10
+        cells = sum(w.cells for w in wls)
+        units = cells * (nt - 1) * stride
+        mu = wls[0].A
+        step = lambda: h.response1_all(mu, mu, nt, stride)
+        desc = ("sweep: %d seeded two-mode instances (grids 24..48 per axis, depth 4), batched: one "
+                "launch per RK4 stage for all; R1 over 2000 steps (201 samples); tiers 3-4 in bf16"
+                % n)
+        unit_name = "R1 responses of the batch"
+    eq_s = time.perf_counter() - t_eq
+    for _ in range(args.warmup):
+        step()
+    clocks = Clocks(local)
+    torch.cuda.synchronize(dev)
+    h.stats_reset(time_stages=args.workload != "one_mode_64")
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    st = h.stats()
+    T = ev0.elapsed_time(ev1) / 1e3
+    achieved = st["stage_bytes"] / (st["stage_ms"] / 1e3) / 1e9 if st["stage_ms"] > 0 else None
+    line = {
+        "metric": "CHFPE cell-updates/s", "value": units * args.steps / T, "unit": "cell-updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "data": "synthetic", "config": {"workload": desc, "equilibration": {"steps": eq[0],
+                                         "residual": eq[1], "seconds": eq_s}},
+        "per_s": {unit_name: args.steps / T},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "peak_kind": peak_kind,
+                     "note": None if achieved else "launch-bound: stage bursts inside CUDA graphs are not timed"},
+        "clocks": clk, "gpu_launches": st["kernel_launches"],
+    }
+    if args.workload == "three_mode_20":
+        line["extrapolated_s_per_128x128_spectrum"] = (inputs.three_mode_20().r2_state_steps() *
+                                                        wl.cells / (units * args.steps / T))
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     args = parse()
     rank, world, local, pg = dist_setup(args.gpus)
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.workload != "two_mode_32":
+            run_extra(args, local)
         else:
             run_ours(args, rank, world, local, pg)
     finally:
