@@ -28,6 +28,9 @@ sys.path.insert(0, ROOT)
 from paper_2509_25840_b300 import inputs  # noqa: E402
 
 ELEM_ACCESSES_PER_CELL_STEP = 11      # Horner-form RK4: 2 + 3 + 3 + 3 element accesses
+# launch shapes of the RK4 stage kernel the library's autotuner chooses from (variant index ->
+# points per thread, threads per block, minimum resident blocks per SM), as in chfpe.cu
+STAGE_SHAPES = {0: (2, 128, 8), 1: (2, 256, 4), 2: (2, 128, 6), 3: (4, 128, 4)}
 
 
 def parse():
@@ -241,6 +244,10 @@ def run_ours(args, rank, world, local, pg):
 
     peak, peak_kind = peaks()
     achieved = st["stage_bytes"] / (st["stage_ms"] / 1e3) / 1e9 if st["stage_ms"] > 0 else None
+    # the launch shape the autotuner picked at create: (points per thread, threads, min blocks)
+    variant, tune_us = h.stage_tuning()
+    V, NT, MINB = STAGE_SHAPES[variant]
+    kernel = "stage_vec_kernel<float,2,4,%d,%d,%d,15>" % (V, NT, MINB)
     # DRAM bytes per launch from the committed ncu capture of this kernel: measured bytes per
     # cell-stage times the cells of one branch-phase launch (nt1 states)
     traffic = None
@@ -249,12 +256,12 @@ def run_ours(args, rank, world, local, pg):
         try:
             tj = json.load(open(prof))
             per_cell = tj.get("bytes_per_cell_stage_two_mode_32")
-            if per_cell and tj.get("kernel") == "stage_vec_kernel<float,2,4,2,128,8>":
+            if per_cell and tj.get("kernel") == kernel:
                 traffic = per_cell * nt1 * wl.cells
         except Exception:
             traffic = None
     roofline = {
-        "kernel": "stage_vec_kernel<float,2,4,2,128,8>",
+        "kernel": kernel,
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
         "traffic": traffic,
@@ -302,7 +309,10 @@ def run_ours(args, rank, world, local, pg):
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (branch arrays 3 x %.1f GB)" % (
                            nt1 * wl.cells * 4 / 1e9),
-                       "equilibration": {"steps": eq_steps, "residual": eq_res, "seconds": eq_s}},
+                       "equilibration": {"steps": eq_steps, "residual": eq_res, "seconds": eq_s},
+                       "stage_shape": {"variant": variant, "points_per_thread": V, "threads": NT,
+                                       "min_blocks_per_sm": MINB,
+                                       "autotune_us_per_launch": [round(u, 1) for u in tune_us]}},
             "spectra_per_s": args.steps * world / T,
             "roofline": roofline,
             "clocks": clk,

@@ -199,6 +199,83 @@ chfpe_status chfpe_observe_noalloc(const chfpe_model *model, const chfpe_grid *g
                                    int precision, const chfpe_optical *C, const void *states,
                                    int batch, double *R_dev, void *stream);
 
+/* ---- learned surrogate of R2 (no counterpart in the paper) -------------------------------------
+ *
+ * A network that maps 12 standardised model parameters to a normalised R2 on a 64 x 64 (t1, t2)
+ * grid and to log10 of its scale, trained on spectra computed by chfpe_response2.  Architecture
+ * (fixed): 4 x [Linear(512) + SiLU] -> h4; scale head s = h4 . w_h + b_h; decoder: h4 read as an
+ * NHWC image 4 x 4 x 32 (feature f -> row f / 128, column f / 32 % 4, channel f % 32), then
+ * 4 x [nearest upsample x2, 3x3 convolution with zero padding 1], channels 32 -> 32 -> 16 -> 8 -> 1,
+ * SiLU after all but the last; output image [64][64] row-major (t1 rows, t2 columns).
+ * Loss = mean over pixels (y - t)^2 + w_scale * mean over the batch (s - t_s)^2.  Every
+ * contraction (forward, data gradient, weight gradient) is a BF16 tensor-core GEMM with FP32
+ * accumulation; master weights, gradients and the AdamW moments (beta1 0.9, beta2 0.999,
+ * eps 1e-8, decoupled weight decay) are FP32.
+ *
+ * Parameter layout on the host (get/set_params, gradients): float[chfpe_surrogate_param_count()],
+ * layers in the order linear 1..4, scale head, conv 1..4, each as its weight [out][in] row-major
+ * followed by its bias [out]; a convolution's "in" index is ci * 9 + ky * 3 + kx (input channel,
+ * tap row, tap column; tap (ky, kx) reads the upsampled input at (y + ky - 1, x + kx - 1)).
+ *
+ * All data pointers below are device pointers (FP32) unless noted; every call runs on the stream
+ * given at create (NULL: a stream of the handle's own) and is asynchronous unless noted.
+ */
+#define CHFPE_SURROGATE_NIN 12
+#define CHFPE_SURROGATE_NOUT 4096
+
+typedef struct chfpe_surrogate chfpe_surrogate;
+
+/* Number of parameters in the host layout above (810,242). */
+long long chfpe_surrogate_param_count(void);
+/* New network with seeded initial weights (uniform +-sqrt(6/fan_in), +-sqrt(1.5/fan_in) for the
+ * two output layers, biases 0), activation buffers for batches up to max_batch (1..4096; about
+ * 3.3 MB of device memory per row).  Synchronous.  CHFPE_EINVAL, CHFPE_ENOMEM, CHFPE_ECUDA. */
+chfpe_status chfpe_surrogate_create(int max_batch, unsigned long long seed, void *stream,
+                                    chfpe_surrogate **out);
+void chfpe_surrogate_destroy(chfpe_surrogate *s);
+/* Copy the FP32 master weights to / from a caller-owned host array in the layout above.  set also
+ * zeroes the AdamW state and its step count.  Synchronous. */
+chfpe_status chfpe_surrogate_get_params(chfpe_surrogate *s, float *host);
+chfpe_status chfpe_surrogate_set_params(chfpe_surrogate *s, const float *host);
+/* Inference: X [n][12] -> Y [n][4096] (normalised R2) and S [n] (log10 scale), in chunks of
+ * max_batch rows. */
+chfpe_status chfpe_surrogate_infer(chfpe_surrogate *s, const float *X, int n, float *Y, float *S);
+/* Loss and gradients of one batch (1 <= n <= max_batch) without an update: targets T [n][4096]
+ * and TS [n]; *loss (host) and grad_host (host, layout above, may be NULL).  Synchronous. */
+chfpe_status chfpe_surrogate_gradients(chfpe_surrogate *s, const float *X, const float *T,
+                                       const float *TS, int n, float w_scale, double *loss,
+                                       float *grad_host);
+/* Training: `epochs` passes over the n samples (X [n][12], T [n][4096], TS [n] resident in device
+ * memory), each a seeded shuffle (SplitMix64, Fisher-Yates) cut into n / batch whole batches, one
+ * AdamW step per batch at learning rate lr.  epoch_loss (host, may be NULL) receives the mean
+ * batch loss of each epoch.  Synchronous. */
+chfpe_status chfpe_surrogate_train(chfpe_surrogate *s, const float *X, const float *T,
+                                   const float *TS, int n, int batch, int epochs, float lr,
+                                   float weight_decay, float w_scale, unsigned long long seed,
+                                   double *epoch_loss);
+/* The GEMM kernel alone (for tests): C[m][n] = sum_k A(m,k) B(n,k) (+ bias[n]) with BF16 A, B
+ * and FP32 C, A(m,k) = ta ? A[k*lda + m] : A[m*lda + k], B(n,k) = tb ? B[k*ldb + n] : B[n*ldb + k],
+ * C row-major [M][N].  splits > 1 splits K and ADDS into C; splits == 1 overwrites C. */
+chfpe_status chfpe_surrogate_gemm(const void *A, int ta, int lda, const void *B, int tb, int ldb,
+                                  float *C, const float *bias, int M, int N, int K, int splits,
+                                  void *stream);
+
+/* ---- stage-kernel autotuning (no counterpart in the paper) ----------------------------------
+ *
+ * The RK4 stage kernel has CHFPE_STAGE_VARIANTS launch shapes (points per thread, threads per
+ * block, register budget).  For FP32 handles with plain storage and the hierarchies
+ * (modes, depth) = (1, 5), (2, 2), (2, 4), (3, 2), chfpe_create times every shape on zeroed
+ * scratch arenas of the handle (up to 4 branch states, else the chain's work arrays; three
+ * launches each after one warm-up) and keeps the fastest; every other handle uses shape 0.
+ * The environment variable CHFPE_STAGE_VARIANT=k (0..3) forces shape k.  Shape 3 needs the last
+ * p extent to be a multiple of 4 and falls back to shape 0 otherwise.  All shapes compute the
+ * same arithmetic in the same order.
+ */
+#define CHFPE_STAGE_VARIANTS 4
+/* The chosen shape and the measured microseconds per stage launch of each shape (-1: not timed);
+ * us may be NULL, else it receives CHFPE_STAGE_VARIANTS doubles. */
+chfpe_status chfpe_stage_tuning(const chfpe_handle *h, int *variant, double *us);
+
 /* ---- counters for measurement (no counterpart in the paper) ---------------------------------- */
 
 typedef struct {

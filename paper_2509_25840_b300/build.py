@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libchfpe.so")
-SOURCES = [os.path.join(HERE, "csrc", "chfpe.cu"), os.path.join(HERE, "csrc", "noalloc.cu")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("chfpe.cu", "noalloc.cu", "surrogate.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "kernels.cuh"), os.path.join(ROOT, "include", "chfpe.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libchfpe.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
+STAGE_VARIANTS = 4
 _NAMES = {0: "CHFPE_OK", 1: "CHFPE_EINVAL", 2: "CHFPE_ENOMEM", 3: "CHFPE_ECUDA",
           4: "CHFPE_EUNSTABLE", 5: "CHFPE_ETIMEOUT", 6: "CHFPE_ESTATE"}
 
@@ -60,6 +61,7 @@ class chfpe_stats(ctypes.Structure):
 
 _lib = None
 _DP = ctypes.POINTER(ctypes.c_double)
+_FP = ctypes.POINTER(ctypes.c_float)
 _VP = ctypes.c_void_p
 _H = ctypes.c_void_p
 
@@ -110,6 +112,20 @@ def load(path: str = LIB_PATH):
         "chfpe_stats_reset": ([_H, ctypes.c_int], S),
         "chfpe_stats_get": ([_H, ctypes.POINTER(chfpe_stats)], S),
         "chfpe_last_error": ([], ctypes.c_char_p),
+        "chfpe_stage_tuning": ([_H, ctypes.POINTER(ctypes.c_int), _DP], S),
+        "chfpe_surrogate_param_count": ([], ctypes.c_longlong),
+        "chfpe_surrogate_create": ([ctypes.c_int, ctypes.c_ulonglong, _VP, ctypes.POINTER(_H)], S),
+        "chfpe_surrogate_destroy": ([_H], None),
+        "chfpe_surrogate_get_params": ([_H, _FP], S),
+        "chfpe_surrogate_set_params": ([_H, _FP], S),
+        "chfpe_surrogate_infer": ([_H, _VP, ctypes.c_int, _VP, _VP], S),
+        "chfpe_surrogate_gradients": ([_H, _VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _DP, _FP], S),
+        "chfpe_surrogate_train": ([_H, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_ulonglong, _DP], S),
+        "chfpe_surrogate_gemm": ([_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int,
+                                  _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  _VP], S),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -295,6 +311,13 @@ class Handle:
                                       int(nt1), int(nt2), int(stride), _dptr(R)))
         return R
 
+    def stage_tuning(self):
+        """(chosen launch shape, microseconds per stage launch of each shape or -1)."""
+        v = ctypes.c_int()
+        us = np.zeros(STAGE_VARIANTS)
+        _check(load().chfpe_stage_tuning(self._h, ctypes.byref(v), _dptr(us)))
+        return v.value, us
+
     # -- device buffers -------------------------------------------------------------------------
     def rhs_device(self, in_ptr: int, out_ptr: int, batch: int = 1):
         _check(load().chfpe_rhs_device(self._h, in_ptr, out_ptr, int(batch)))
@@ -366,3 +389,83 @@ class Batch(Handle):
             if w is not None:
                 w._h = None
         super().close()
+
+
+# ------------------------------------------------------------------------------------------
+# learned surrogate (chfpe_surrogate_*): device pointers are passed as integers
+# ------------------------------------------------------------------------------------------
+
+SURROGATE_NIN, SURROGATE_NOUT = 12, 4096
+
+
+def surrogate_param_count() -> int:
+    return int(load().chfpe_surrogate_param_count())
+
+
+def surrogate_gemm(A_ptr: int, ta: bool, lda: int, B_ptr: int, tb: bool, ldb: int, C_ptr: int,
+                   bias_ptr: int | None, M: int, N: int, K: int, splits: int = 1,
+                   stream: int | None = None):
+    """chfpe_surrogate_gemm: the BF16 tensor-core GEMM alone (BF16 A, B; FP32 C and bias)."""
+    _check(load().chfpe_surrogate_gemm(A_ptr, int(bool(ta)), int(lda), B_ptr, int(bool(tb)),
+                                       int(ldb), C_ptr, bias_ptr, int(M), int(N), int(K),
+                                       int(splits), stream))
+
+
+class Surrogate:
+    """chfpe_surrogate: the 12 -> 64 x 64 network, its training and inference on the device."""
+
+    def __init__(self, max_batch: int = 256, seed: int = 1, stream: int | None = None):
+        h = _H()
+        _check(load().chfpe_surrogate_create(int(max_batch), int(seed), stream, ctypes.byref(h)))
+        self._h = h
+        self.max_batch = int(max_batch)
+        self.stream = stream          # cudaStream_t the calls run on (None: the handle's own)
+        self.nparam = surrogate_param_count()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().chfpe_surrogate_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(load().chfpe_surrogate_get_params(self._h, out.ctypes.data_as(_FP)))
+        return out
+
+    def set_params(self, flat: np.ndarray):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        if a.size != self.nparam:
+            raise ValueError(f"expected {self.nparam} parameters, got {a.size}")
+        _check(load().chfpe_surrogate_set_params(self._h, a.ctypes.data_as(_FP)))
+
+    def infer(self, X_ptr: int, n: int, Y_ptr: int, S_ptr: int):
+        _check(load().chfpe_surrogate_infer(self._h, X_ptr, int(n), Y_ptr, S_ptr))
+
+    def gradients(self, X_ptr: int, T_ptr: int, TS_ptr: int, n: int, w_scale: float = 1.0,
+                  want_grads: bool = True):
+        loss = ctypes.c_double()
+        g = np.empty(self.nparam, dtype=np.float32) if want_grads else None
+        _check(load().chfpe_surrogate_gradients(self._h, X_ptr, T_ptr, TS_ptr, int(n),
+                                                float(w_scale), ctypes.byref(loss),
+                                                g.ctypes.data_as(_FP) if want_grads else None))
+        return loss.value, g
+
+    def train(self, X_ptr: int, T_ptr: int, TS_ptr: int, n: int, batch: int, epochs: int,
+              lr: float, weight_decay: float = 0.0, w_scale: float = 1.0, seed: int = 0):
+        losses = np.zeros(max(int(epochs), 1), dtype=np.float64)
+        _check(load().chfpe_surrogate_train(self._h, X_ptr, T_ptr, TS_ptr, int(n), int(batch),
+                                            int(epochs), float(lr), float(weight_decay),
+                                            float(w_scale), int(seed), _dptr(losses)))
+        return losses[:int(epochs)]

@@ -90,6 +90,8 @@ struct chfpe_handle {
     double stage_bytes = 0.0, cell_updates = 0.0;
     bool time_stages = false;
     bool force_scalar = false;          // CHFPE_SCALAR_STAGE=1: one point per thread (V = 1)
+    int variant = 0;                    // stage launch shape (kStageVariants), set by autotune()
+    double tune_us[CHFPE_STAGE_VARIANTS] = {};   // measured us per launch, -1 = not available
     std::vector<cudaEvent_t> ev;        // pairs (start, stop) of timed bursts
     size_t ev_used = 0;
 
@@ -159,36 +161,60 @@ static int bf16_m32(int d, int depth, int tier) {
     return -1;
 }
 
+// Launch shapes the autotuner chooses from (FP32, plain storage, the workload hierarchies
+// (d, depth) = (1, 5), (2, 2), (2, 4), (3, 2); every other configuration uses shape 0):
+//   0  2 points per thread, 128 threads, registers for 8 blocks per SM (4 beyond 15 members)
+//   1  2 points per thread, 256 threads, same registers per thread (more p_1 rows per block)
+//   2  2 points per thread, 128 threads, registers for 6 blocks per SM (fewer spills)
+//   3  4 points per thread, 128 threads, registers for 4 blocks per SM (needs n_pd % 4 == 0)
+constexpr bool tunable(int T_size, int D, int DEPTH) {
+    return T_size == 4 && ((D == 1 && DEPTH == 5) || (D == 2 && (DEPTH == 2 || DEPTH == 4)) ||
+                           (D == 3 && DEPTH == 2));
+}
+
+template <typename T, int D, int DEPTH, int M32, int V, int NT, int MINB>
+static void launch_vec(const StageArgs<T> &a, int batch, cudaStream_t s) {
+    const int nthr = a.g.P / V;
+    stage_vec_kernel<T, D, DEPTH, V, NT, MINB, M32><<<dim3((nthr + NT - 1) / NT, batch), NT, 0, s>>>(a);
+}
+
 template <typename T, int D, int DEPTH, int M32>
-static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, cudaStream_t s) {
+static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int variant, cudaStream_t s) {
     constexpr int M = member_count(D, DEPTH);
     constexpr int MINB = (sizeof(T) == 4 && M <= 15) ? 8 : 4;
-    if (vec) {
-        const int nthr = a.g.P / kVec;
-        stage_vec_kernel<T, D, DEPTH, kVec, 128, MINB, M32>
-            <<<dim3((nthr + 127) / 128, batch), 128, 0, s>>>(a);
-    } else {
+    if (!vec) {
         stage_vec_kernel<T, D, DEPTH, 1, 128, 4, M32>
             <<<dim3((a.g.P + 127) / 128, batch), 128, 0, s>>>(a);
+        return;
     }
+    if constexpr (tunable(sizeof(T), D, DEPTH) && M32 == M) {
+        switch (variant) {
+        case 1: launch_vec<T, D, DEPTH, M32, 2, 256, MINB / 2>(a, batch, s); return;
+        case 2: launch_vec<T, D, DEPTH, M32, 2, 128, 6>(a, batch, s); return;
+        case 3: launch_vec<T, D, DEPTH, M32, 4, 128, 4>(a, batch, s); return;
+        default: break;
+        }
+    }
+    launch_vec<T, D, DEPTH, M32, kVec, 128, MINB>(a, batch, s);
 }
 
 template <typename T, int D, int DEPTH>
-static bool launch_stage_t(const StageArgs<T> &a, int batch, bool vec, int M32, cudaStream_t s) {
+static bool launch_stage_t(const StageArgs<T> &a, int batch, bool vec, int M32, int variant,
+                           cudaStream_t s) {
     constexpr int M = member_count(D, DEPTH);
     if (M32 == M) {
-        launch_stage_m<T, D, DEPTH, M>(a, batch, vec, s);
+        launch_stage_m<T, D, DEPTH, M>(a, batch, vec, variant, s);
         return true;
     }
     if constexpr (sizeof(T) == 4 && D == 2 && DEPTH == 4) {
         if (M32 == 6) {
-            launch_stage_m<T, D, DEPTH, 6>(a, batch, vec, s);
+            launch_stage_m<T, D, DEPTH, 6>(a, batch, vec, 0, s);
             return true;
         }
     }
     if constexpr (sizeof(T) == 4 && D == 3 && DEPTH == 2) {
         if (M32 == 4) {
-            launch_stage_m<T, D, DEPTH, 4>(a, batch, vec, s);
+            launch_stage_m<T, D, DEPTH, 4>(a, batch, vec, 0, s);
             return true;
         }
     }
@@ -202,8 +228,10 @@ static bool launch_stage(const chfpe_handle *h, const StageArgs<T> &a, int batch
     cudaStream_t s = h->stream;
     const bool vec = (h->n[2 * h->d - 1] % kVec == 0) && aligned16(a.in) && aligned16(a.y) &&
                      aligned16(a.out) && !h->force_scalar;
+    // shape 3 reads 4 consecutive p_d points: only where rows hold whole groups of 4
+    const int variant = (h->variant == 3 && h->n[2 * h->d - 1] % 4 != 0) ? 0 : h->variant;
 #define CASE(D_, K_) \
-    case (D_ * 16 + K_): return launch_stage_t<T, D_, K_>(a, batch, vec, m32, s);
+    case (D_ * 16 + K_): return launch_stage_t<T, D_, K_>(a, batch, vec, m32, variant, s);
     const int m32 = sizeof(T) == 8 ? h->M : h->M32;
     switch (h->d * 16 + h->depth) {
         CASE(1, 0) CASE(1, 1) CASE(1, 2) CASE(1, 3) CASE(1, 4) CASE(1, 5) CASE(1, 6) CASE(1, 7)
@@ -581,6 +609,8 @@ extern "C" void chfpe_destroy(chfpe_handle *h) {
     delete h;
 }
 
+static chfpe_status autotune(chfpe_handle *h);
+
 static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid,
                                 const chfpe_options *opts, bool borrowed, chfpe_handle **out) {
     if (!out) return fail(CHFPE_EINVAL, "out is null");
@@ -701,7 +731,71 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
     e = cudaGetLastError();
     if (!e) e = cudaStreamSynchronize(h->stream);
     if (e) { chfpe_destroy(h); return fail(CHFPE_ECUDA, cudaGetErrorString(e)); }
+    if (!borrowed && (st = autotune(h))) { chfpe_destroy(h); return st; }
     *out = h;
+    return CHFPE_OK;
+}
+
+// Stage-kernel autotuner: times every launch shape available for this handle's configuration on
+// zeroed scratch arenas (up to 4 branch states, else the chain's two work arrays) and keeps the
+// fastest.  CHFPE_STAGE_VARIANT=k in the environment forces shape k instead.
+static chfpe_status autotune(chfpe_handle *h) {
+    for (double &u : h->tune_us) u = -1.0;
+    h->variant = 0;
+    const char *env = getenv("CHFPE_STAGE_VARIANT");
+    if (env && env[0]) {
+        const int v = atoi(env);
+        if (v >= 0 && v < CHFPE_STAGE_VARIANTS) h->variant = v;
+        return CHFPE_OK;
+    }
+    const int npd = h->n[2 * h->d - 1];
+    if (h->prec != 32 || h->M32 != h->M || !tunable(4, h->d, h->depth) || h->force_scalar ||
+        npd % kVec != 0)
+        return CHFPE_OK;
+    char *in = (char *)(h->ba ? h->ba : h->ca);
+    char *out = (char *)(h->bb ? h->bb : h->cb);
+    const int batch = h->ba ? std::min(h->opts.max_batch, 4) : 1;
+    CK(cudaMemsetAsync(in, 0, (size_t)h->state_bytes * batch, h->stream));
+    CK(cudaMemsetAsync(out, 0, (size_t)h->state_bytes * batch, h->stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(CHFPE_ECUDA, "event create"); }
+    StageArgs<float> a = stage_args<float>(h);
+    a.in = in;
+    a.y = out;
+    a.out = out;
+    a.c = 1e-3f;
+    int best = 0;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < CHFPE_STAGE_VARIANTS && e == cudaSuccess; ++v) {
+        if (v == 3 && npd % 4 != 0) continue;
+        h->variant = v;
+        launch_stage<float>(h, a, batch);   // warm-up
+        e = cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            launch_stage<float>(h, a, batch);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        h->tune_us[v] = 1e3 * ms / 3.0;
+        if (h->tune_us[v] < h->tune_us[best]) best = v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->variant = best;
+    if (e != cudaSuccess) return fail(CHFPE_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_stage_tuning(const chfpe_handle *h, int *variant, double *us) {
+    if (!h) return fail(CHFPE_EINVAL, "null handle");
+    if (variant) *variant = h->variant;
+    if (us)
+        for (int v = 0; v < CHFPE_STAGE_VARIANTS; ++v) us[v] = h->tune_us[v];
     return CHFPE_OK;
 }
 

@@ -317,3 +317,29 @@ def random_state(grid: Grid, nmembers: int, seed: int, smooth: bool = True) -> n
         else:
             out[i] = env * uniform_array(seed * 1000003 + i, grid.points).reshape(grid.shape)
     return out
+
+
+# ------------------------------------------------------------------------------------------
+# the surrogate's parameter space: the sweep's uniform ranges, 12 parameters per instance
+# ------------------------------------------------------------------------------------------
+
+SURROGATE_NAMES = ("omega_1", "omega_2", "g4_1", "g4_2", "zeta_1", "zeta_2", "gamma_1",
+                   "gamma_2", "kT", "g_12^2", "V_SL/V_LL_1", "V_SL/V_LL_2")
+SURROGATE_LO = np.array([0.5, 0.5, 0.0, 0.0, 0.05, 0.05, 0.5, 0.5, 0.5, 0.0, 0.0, 0.0])
+SURROGATE_HI = np.array([2.0, 2.0, 0.05, 0.05, 1.0, 1.0, 3.0, 3.0, 2.0, 0.3, 0.5, 0.5])
+
+
+def surrogate_params(seed: int) -> np.ndarray:
+    """Seeded draw of the 12 parameters, each uniform in its range (SplitMix64 stream `seed`)."""
+    u = uniform_array(seed * 7919 + 17, 12, 0.0, 1.0)
+    return SURROGATE_LO + u * (SURROGATE_HI - SURROGATE_LO)
+
+
+def surrogate_model(x) -> Model:
+    """The two-mode model of a 12-parameter vector (m = 1, V_LL = 1, the other couplings 0)."""
+    x = [float(v) for v in x]
+    g_ss2 = np.zeros((3, 3))
+    g_ss2[0, 1] = x[9]
+    return Model(nmodes=2, kT=x[8], m=(1.0, 1.0), omega=(x[0], x[1]), g4=(x[2], x[3]),
+                 g_ss2=g_ss2, zeta=(x[4], x[5]), gamma=(x[6], x[7]), V_LL=(1.0, 1.0),
+                 V_SL=(x[10], x[11]))

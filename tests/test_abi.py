@@ -54,3 +54,17 @@ def test_create_rejects_invalid_arguments_on_cpu():
     small = inputs.Grid(nq=(6,), np=(64,), qmin=(-6,), qmax=(6,), pmin=(-6,), pmax=(6,))
     with pytest.raises(chfpe.ChfpeError):
         chfpe.Handle(wl.model, small, depth=2, dt=0.005)
+
+
+def test_surrogate_host_entry_points_on_cpu():
+    """Parameter count agrees with the oracle's layer list; create rejects bad sizes before
+    touching a device."""
+    import ctypes
+    from oracle import surrogate_oracle as so
+    from paper_2509_25840_b300 import chfpe
+    lib = chfpe.load()
+    assert lib.chfpe_surrogate_param_count() == so.param_count()
+    h = ctypes.c_void_p()
+    for bad in (0, -3, 4097):
+        assert lib.chfpe_surrogate_create(bad, 1, None, ctypes.byref(h)) == chfpe.EINVAL
+        assert not h.value

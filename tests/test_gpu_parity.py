@@ -268,3 +268,40 @@ def test_vector_and_scalar_stage_kernels_agree(prec, monkeypatch):
             outs.append(y.double().cpu().numpy())
     scale = np.abs(outs[0]).max()
     assert np.abs(outs[0] - outs[1]).max() <= (1e-14 if prec == 64 else 1e-6) * scale
+
+
+TUNED_CASES = [(1, [40, 48], 5), (2, [9, 11, 12, 16], 4), (2, [9, 11, 13, 12], 2),
+               (3, [7, 8, 9, 7, 8, 12], 2)]
+
+
+@pytest.mark.parametrize("variant", range(4))
+@pytest.mark.parametrize("d,n,depth", TUNED_CASES)
+def test_every_stage_launch_shape_matches_oracle(d, n, depth, variant, monkeypatch):
+    """Each launch shape the autotuner can pick (forced through CHFPE_STAGE_VARIANT), FP32,
+    against the oracle's RHS: same bar as the other FP32 RHS cases."""
+    monkeypatch.setenv("CHFPE_STAGE_VARIANT", str(variant))
+    model, grid, h, pb = _setup(d, n, depth, 32)
+    with h:
+        assert h.stage_tuning()[0] == variant
+        W = _rounded(inputs.random_state(grid, pb.M, seed=300 + d, smooth=False), 32)
+        want = oracle.rhs(pb, W)
+        x = torch.tensor(W, dtype=torch.float32, device="cuda")
+        y = torch.empty_like(x)
+        h.rhs_device(x.data_ptr(), y.data_ptr(), 1)
+        got = y.double().cpu().numpy()
+    assert np.abs(got - want).max() <= 3e-6 * np.abs(want).max()
+
+
+def test_autotuner_times_the_shapes_and_keeps_the_fastest(monkeypatch):
+    monkeypatch.delenv("CHFPE_STAGE_VARIANT", raising=False)
+    model = _model(2)
+    grid = inputs.default_grid(model, [16, 16, 16, 16], cut=12.0, nsigma=5.0)
+    chfpe = _chfpe()
+    with chfpe.Handle(model, grid, depth=4, dt=0.004, precision=32, max_batch=4) as h:
+        v, us = h.stage_tuning()
+    print(f"stage shapes (us per launch, 4 states of 16^4 x 15): {np.round(us, 1)} -> {v}")
+    assert np.all(us > 0)
+    assert us[v] == us.min()
+    with chfpe.Handle(model, grid, depth=4, dt=0.004, precision=64) as h:   # not tuned
+        v, us = h.stage_tuning()
+    assert v == 0 and np.all(us == -1)
