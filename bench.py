@@ -30,7 +30,7 @@ from paper_2509_25840_b300 import inputs  # noqa: E402
 ELEM_ACCESSES_PER_CELL_STEP = 11      # Horner-form RK4: 2 + 3 + 3 + 3 element accesses
 # launch shapes of the RK4 stage kernel the library's autotuner chooses from (variant index ->
 # points per thread, threads per block, minimum resident blocks per SM), as in chfpe.cu
-STAGE_SHAPES = {0: (2, 128, 8), 1: (2, 256, 4), 2: (2, 128, 6), 3: (4, 128, 4)}
+STAGE_SHAPES = {0: (2, 128, 8), 1: (2, 256, 4), 2: (2, 128, 6), 3: (4, 128, 4), 4: (4, 128, 4), 5: (4, 128, 4)}
 
 
 def parse():
@@ -247,7 +247,8 @@ def run_ours(args, rank, world, local, pg):
     # the launch shape the autotuner picked at create: (points per thread, threads, min blocks)
     variant, tune_us = h.stage_tuning()
     V, NT, MINB = STAGE_SHAPES[variant]
-    kernel = "stage_vec_kernel<float,2,4,%d,%d,%d,15>" % (V, NT, MINB)
+    kernel = ("stage_bulk_kernel<4,128>" if variant == 4 else "stage_cpasync_kernel<4,128>" if variant == 5 else
+              "stage_vec_kernel<float,2,4,%d,%d,%d,15>" % (V, NT, MINB))
     # DRAM bytes per launch from the committed ncu capture of this kernel: measured bytes per
     # cell-stage times the cells of one branch-phase launch (nt1 states)
     traffic = None

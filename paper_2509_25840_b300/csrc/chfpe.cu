@@ -3,6 +3,7 @@
 // kernels.cuh; host code here validates, sizes, launches and copies.
 #include "../../include/chfpe.h"
 #include "kernels.cuh"
+#include "bulk.cuh"
 
 #include <cuda_runtime.h>
 
@@ -90,6 +91,7 @@ struct chfpe_handle {
     double stage_bytes = 0.0, cell_updates = 0.0;
     bool time_stages = false;
     bool force_scalar = false;          // CHFPE_SCALAR_STAGE=1: one point per thread (V = 1)
+    int *d_err = nullptr;               // device error word of the bounded waits (bulk stage)
     int variant = 0;                    // stage launch shape (kStageVariants), set by autotune()
     double tune_us[CHFPE_STAGE_VARIANTS] = {};   // measured us per launch, -1 = not available
     std::vector<cudaEvent_t> ev;        // pairs (start, stop) of timed bursts
@@ -102,8 +104,9 @@ struct chfpe_handle {
     std::vector<long long> inst_off;    // byte offset of each instance in the batch arenas
     int nsub = 1;                       // RK4 substeps per requested step (dt / nsub per step)
     void *d_geo = nullptr;              // InstGeo<T>[n]
-    int2 *d_work_vec = nullptr, *d_work_sc = nullptr;
-    int nwork_vec = 0, nwork_sc = 0;
+    // work lists by tile shape: [0] 4 points per thread, [1] 2 points, [2] 1 point
+    int2 *d_work[3] = {nullptr, nullptr, nullptr};
+    int nwork[3] = {0, 0, 0};
     double cells_total = 0.0;
 };
 
@@ -167,6 +170,9 @@ static int bf16_m32(int d, int depth, int tier) {
 //   1  2 points per thread, 256 threads, same registers per thread (more p_1 rows per block)
 //   2  2 points per thread, 128 threads, registers for 6 blocks per SM (fewer spills)
 //   3  4 points per thread, 128 threads, registers for 4 blocks per SM (needs n_pd % 4 == 0)
+//   4  shape 3 with every member's tile staged in shared memory by bulk async copies, double
+//      buffered across members (two modes only; bulk.cuh)
+//   5  shape 4 with the buffers filled by every thread's 16-byte cp.async copies
 constexpr bool tunable(int T_size, int D, int DEPTH) {
     return T_size == 4 && ((D == 1 && DEPTH == 5) || (D == 2 && (DEPTH == 2 || DEPTH == 4)) ||
                            (D == 3 && DEPTH == 2));
@@ -178,8 +184,36 @@ static void launch_vec(const StageArgs<T> &a, int batch, cudaStream_t s) {
     stage_vec_kernel<T, D, DEPTH, V, NT, MINB, M32><<<dim3((nthr + NT - 1) / NT, batch), NT, 0, s>>>(a);
 }
 
+constexpr int kBulkNT = 128, kBulkTP = kBulkNT * 4;
+
+static BulkArgs bulk_args(const Geo<float> &g, int *err) {
+    BulkArgs b;
+    b.tiles_per_plane = (g.Pp + kBulkTP - 1) / kBulkTP;
+    b.H = 3 * g.n[3];
+    b.buf_floats = kBulkTP + 2 * b.H + 12 * kBulkTP;
+    b.err = err;
+    return b;
+}
+
+static bool bulk_ok(const Geo<float> &g) { return g.n[3] % 4 == 0; }
+
+// shapes 4 (bulk async copies) and 5 (16-byte cp.async) of two-mode hierarchies
+template <int DEPTH, bool CPASYNC>
+static void launch_bulk(const StageArgs<float> &a, int batch, int *err, cudaStream_t s) {
+    const BulkArgs b = bulk_args(a.g, err);
+    const size_t smem = (size_t)2 * b.buf_floats * sizeof(float);
+    auto kern = CPASYNC ? stage_cpasync_kernel<DEPTH, kBulkNT> : stage_bulk_kernel<DEPTH, kBulkNT>;
+    static size_t configured = 0;   // largest dynamic shared memory opted into so far
+    if (smem > configured) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = smem;
+    }
+    kern<<<dim3(a.g.NQ * b.tiles_per_plane, batch), kBulkNT, smem, s>>>(a, b);
+}
+
 template <typename T, int D, int DEPTH, int M32>
-static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int variant, cudaStream_t s) {
+static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int variant, int *err,
+                           cudaStream_t s) {
     constexpr int M = member_count(D, DEPTH);
     constexpr int MINB = (sizeof(T) == 4 && M <= 15) ? 8 : 4;
     if (!vec) {
@@ -192,6 +226,16 @@ static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int varia
         case 1: launch_vec<T, D, DEPTH, M32, 2, 256, MINB / 2>(a, batch, s); return;
         case 2: launch_vec<T, D, DEPTH, M32, 2, 128, 6>(a, batch, s); return;
         case 3: launch_vec<T, D, DEPTH, M32, 4, 128, 4>(a, batch, s); return;
+        case 4:
+        case 5:
+            if constexpr (D == 2) {
+                if (bulk_ok(a.g)) {
+                    if (variant == 4) launch_bulk<DEPTH, false>(a, batch, err, s);
+                    else launch_bulk<DEPTH, true>(a, batch, err, s);
+                    return;
+                }
+            }
+            break;
         default: break;
         }
     }
@@ -200,21 +244,21 @@ static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int varia
 
 template <typename T, int D, int DEPTH>
 static bool launch_stage_t(const StageArgs<T> &a, int batch, bool vec, int M32, int variant,
-                           cudaStream_t s) {
+                           int *err, cudaStream_t s) {
     constexpr int M = member_count(D, DEPTH);
     if (M32 == M) {
-        launch_stage_m<T, D, DEPTH, M>(a, batch, vec, variant, s);
+        launch_stage_m<T, D, DEPTH, M>(a, batch, vec, variant, err, s);
         return true;
     }
     if constexpr (sizeof(T) == 4 && D == 2 && DEPTH == 4) {
         if (M32 == 6) {
-            launch_stage_m<T, D, DEPTH, 6>(a, batch, vec, 0, s);
+            launch_stage_m<T, D, DEPTH, 6>(a, batch, vec, 0, err, s);
             return true;
         }
     }
     if constexpr (sizeof(T) == 4 && D == 3 && DEPTH == 2) {
         if (M32 == 4) {
-            launch_stage_m<T, D, DEPTH, 4>(a, batch, vec, 0, s);
+            launch_stage_m<T, D, DEPTH, 4>(a, batch, vec, 0, err, s);
             return true;
         }
     }
@@ -228,10 +272,10 @@ static bool launch_stage(const chfpe_handle *h, const StageArgs<T> &a, int batch
     cudaStream_t s = h->stream;
     const bool vec = (h->n[2 * h->d - 1] % kVec == 0) && aligned16(a.in) && aligned16(a.y) &&
                      aligned16(a.out) && !h->force_scalar;
-    // shape 3 reads 4 consecutive p_d points: only where rows hold whole groups of 4
-    const int variant = (h->variant == 3 && h->n[2 * h->d - 1] % 4 != 0) ? 0 : h->variant;
+    // shapes 3 and 4 read 4 consecutive p_d points: only where rows hold whole groups of 4
+    const int variant = (h->variant >= 3 && h->n[2 * h->d - 1] % 4 != 0) ? 0 : h->variant;
 #define CASE(D_, K_) \
-    case (D_ * 16 + K_): return launch_stage_t<T, D_, K_>(a, batch, vec, m32, variant, s);
+    case (D_ * 16 + K_): return launch_stage_t<T, D_, K_>(a, batch, vec, m32, variant, h->d_err, s);
     const int m32 = sizeof(T) == 8 ? h->M : h->M32;
     switch (h->d * 16 + h->depth) {
         CASE(1, 0) CASE(1, 1) CASE(1, 2) CASE(1, 3) CASE(1, 4) CASE(1, 5) CASE(1, 6) CASE(1, 7)
@@ -255,6 +299,20 @@ static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *
     if (!launch_stage<T>(h, a, batch)) return fail(CHFPE_EINVAL, "unsupported (d, depth)");
     CK(cudaGetLastError());
     ++h->launches;
+    return CHFPE_OK;
+}
+
+// the bulk stage kernel's bounded waits report through h->d_err: read (and clear) it after a
+// synchronisation of the handle's stream
+static chfpe_status check_device_error(chfpe_handle *h) {
+    if (!h->d_err) return CHFPE_OK;
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, h->d_err, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (v) {
+        CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+        return fail(CHFPE_ETIMEOUT, "a bounded wait of the bulk-copy stage kernel gave up");
+    }
     return CHFPE_OK;
 }
 
@@ -601,7 +659,7 @@ extern "C" void chfpe_destroy(chfpe_handle *h) {
     if (h->borrowed_arenas) h->cy = h->ca = h->cb = h->eq = nullptr;
     void *ptrs[] = {h->U_d, h->F_d, h->F_f, h->wp, h->CWq, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
                     h->cy, h->ca, h->cb, h->by, h->ba, h->bb, h->eq, h->stage64, h->partial, h->dR,
-                    h->counter, h->d_geo, h->d_work_vec, h->d_work_sc};
+                    h->counter, h->d_err, h->d_geo, h->d_work[0], h->d_work[1], h->d_work[2]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -694,6 +752,7 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
     if (h->partial_cap < 4096) h->partial_cap = 4096;
     h->partial = dalloc<double>(h->partial_cap, &st);
     h->counter = dalloc<int>(1, &st);
+    h->d_err = dalloc<int>(1, &st);
     {
         const char *eg = getenv("CHFPE_GRAPHS");
         if (eg) h->use_graphs = atoi(eg);
@@ -718,6 +777,7 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
         inv2m[s] = 0.5 / model->m[s];
     }
     cudaError_t e = cudaSuccess;
+    if (!e) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
     if (!e) e = cudaMemcpyAsync(h->np_d, npv, sizeof npv, cudaMemcpyHostToDevice, h->stream);
     if (!e) e = cudaMemcpyAsync(h->plo_d, plo, sizeof plo, cudaMemcpyHostToDevice, h->stream);
     if (!e) e = cudaMemcpyAsync(h->ph_d, ph, sizeof ph, cudaMemcpyHostToDevice, h->stream);
@@ -765,25 +825,41 @@ static chfpe_status autotune(chfpe_handle *h) {
     a.y = out;
     a.out = out;
     a.c = 1e-3f;
-    int best = 0;
+    // three interleaved rounds of (warm-up, 2 timed launches) per shape; the minimum counts
     cudaError_t e = cudaSuccess;
-    for (int v = 0; v < CHFPE_STAGE_VARIANTS && e == cudaSuccess; ++v) {
-        if (v == 3 && npd % 4 != 0) continue;
-        h->variant = v;
-        launch_stage<float>(h, a, batch);   // warm-up
-        e = cudaEventRecord(e0, h->stream);
-        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
-            launch_stage<float>(h, a, batch);
-            e = cudaGetLastError();
+    for (int round = 0; round < 3 && e == cudaSuccess; ++round) {
+        for (int v = 0; v < CHFPE_STAGE_VARIANTS && e == cudaSuccess; ++v) {
+            if (v >= 3 && npd % 4 != 0) continue;
+            if (v >= 4 && h->d != 2) continue;
+            if (round > 0 && h->tune_us[v] < 0) continue;   // disqualified in an earlier round
+            h->variant = v;
+            launch_stage<float>(h, a, batch);   // warm-up
+            e = cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+                launch_stage<float>(h, a, batch);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            if (v == 4) {   // a bounded wait that gave up disqualifies the shape
+                int bad = 0;
+                e = cudaMemcpy(&bad, h->d_err, sizeof bad, cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess && bad) {
+                    h->tune_us[v] = -1.0;
+                    e = cudaMemset(h->d_err, 0, sizeof(int));
+                    continue;
+                }
+            }
+            const double us = 1e3 * ms / 2.0;
+            if (round == 0 || us < h->tune_us[v]) h->tune_us[v] = us;
         }
-        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) break;
-        h->tune_us[v] = 1e3 * ms / 3.0;
-        if (h->tune_us[v] < h->tune_us[best]) best = v;
     }
+    int best = 0;
+    for (int v = 1; v < CHFPE_STAGE_VARIANTS; ++v)
+        if (h->tune_us[v] > 0 && h->tune_us[v] < h->tune_us[best]) best = v;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->variant = best;
@@ -890,7 +966,7 @@ extern "C" chfpe_status chfpe_propagate(chfpe_handle *h, long nsteps) {
     chfpe_status st = rk4_any(h, h->cy, h->ca, h->cb, 1, nsteps);
     if (st) return st;
     CK(cudaStreamSynchronize(h->stream));
-    return CHFPE_OK;
+    return check_device_error(h);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -993,6 +1069,8 @@ static chfpe_status ensure_dR(chfpe_handle *h, size_t n) {
 static chfpe_status finish_response(chfpe_handle *h, double *R, size_t n) {
     CK(cudaMemcpyAsync(R, h->dR, n * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    chfpe_status st = check_device_error(h);
+    if (st) return st;
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(R[i])) return fail(CHFPE_EUNSTABLE, "non-finite response value");
     return CHFPE_OK;
@@ -1107,7 +1185,7 @@ extern "C" chfpe_status chfpe_rhs_device(chfpe_handle *h, const void *in, void *
                                     : stage<float>(h, in, nullptr, out, 1.0, batch);
     if (st) return st;
     CK(cudaStreamSynchronize(h->stream));
-    return CHFPE_OK;
+    return check_device_error(h);
 }
 
 extern "C" chfpe_status chfpe_rk4_device(chfpe_handle *h, void *states, int batch, long nsteps) {
@@ -1116,7 +1194,7 @@ extern "C" chfpe_status chfpe_rk4_device(chfpe_handle *h, void *states, int batc
     chfpe_status st = rk4_any(h, states, h->ba, h->bb, batch, nsteps);
     if (st) return st;
     CK(cudaStreamSynchronize(h->stream));
-    return CHFPE_OK;
+    return check_device_error(h);
 }
 
 extern "C" chfpe_status chfpe_insert_device(chfpe_handle *h, const chfpe_optical *X, const void *in,
@@ -1256,19 +1334,31 @@ static double bound_for(const chfpe_model *model, const chfpe_grid *grid, int de
     return spectral_bound(&t);
 }
 
+// one launch per non-empty work list (4-, 2- and 1-point tiles); the 4-point list exists only
+// for FP32 hierarchies the autotuner covers
 template <typename T, int D, int DEPTH, int M32>
 static void launch_batch_m(const chfpe_handle *b, const BatchStageArgs<T> &a0) {
     constexpr int M = member_count(D, DEPTH);
     constexpr int MINB = (sizeof(T) == 4 && M <= 15) ? 8 : 4;
     BatchStageArgs<T> a = a0;
-    if (b->nwork_vec) {
-        a.work = b->d_work_vec;
-        stage_batch_kernel<T, D, DEPTH, kVec, 128, MINB, M32><<<b->nwork_vec, 128, 0, b->stream>>>(a);
+    if constexpr (tunable(sizeof(T), D, DEPTH)) {
+        if (b->nwork[0]) {
+            a.work = b->d_work[0];
+            stage_batch_kernel<T, D, DEPTH, 4, 128, 4, M32><<<b->nwork[0], 128, 0, b->stream>>>(a);
+        }
     }
-    if (b->nwork_sc) {
-        a.work = b->d_work_sc;
-        stage_batch_kernel<T, D, DEPTH, 1, 128, 4, M32><<<b->nwork_sc, 128, 0, b->stream>>>(a);
+    if (b->nwork[1]) {
+        a.work = b->d_work[1];
+        stage_batch_kernel<T, D, DEPTH, kVec, 128, MINB, M32><<<b->nwork[1], 128, 0, b->stream>>>(a);
     }
+    if (b->nwork[2]) {
+        a.work = b->d_work[2];
+        stage_batch_kernel<T, D, DEPTH, 1, 128, 4, M32><<<b->nwork[2], 128, 0, b->stream>>>(a);
+    }
+}
+
+static int batch_lists(const chfpe_handle *b) {
+    return (b->nwork[0] ? 1 : 0) + (b->nwork[1] ? 1 : 0) + (b->nwork[2] ? 1 : 0);
 }
 
 template <typename T, int D, int DEPTH>
@@ -1307,7 +1397,7 @@ static chfpe_status batch_stage(chfpe_handle *b, const void *in, const void *y, 
 #undef CASE
     if (!ok) return fail(CHFPE_EINVAL, "unsupported (d, depth, bf16 tier) for batches");
     CK(cudaGetLastError());
-    b->launches += (b->nwork_vec ? 1 : 0) + (b->nwork_sc ? 1 : 0);
+    b->launches += batch_lists(b);
     return CHFPE_OK;
 }
 
@@ -1328,38 +1418,98 @@ static chfpe_status batch_rk4(chfpe_handle *b, long nsteps) {
     for (chfpe_handle *c : b->inst) bytes += (double)c->state_bytes;
     b->cell_updates += (double)nsteps * b->cells_total;
     if (b->time_stages) {
-        b->stage_launches += 4 * nsteps * ((b->nwork_vec ? 1 : 0) + (b->nwork_sc ? 1 : 0));
+        b->stage_launches += 4 * nsteps * batch_lists(b);
         b->stage_bytes += (double)nsteps * bytes * 11.0;
     }
     return CHFPE_OK;
 }
 
+// upload work list k (reallocating its device array)
+static chfpe_status set_work(chfpe_handle *b, int k, const std::vector<int2> &w) {
+    if (b->d_work[k]) cudaFree(b->d_work[k]);
+    b->d_work[k] = nullptr;
+    b->nwork[k] = (int)w.size();
+    if (w.empty()) return CHFPE_OK;
+    chfpe_status st = CHFPE_OK;
+    b->d_work[k] = dalloc<int2>(w.size(), &st);
+    if (st) return st;
+    CK(cudaMemcpyAsync(b->d_work[k], w.data(), w.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    return CHFPE_OK;
+}
+
+// Size classes of the batch: instances whose last p extent is a multiple of 4, of 2, or odd.
+// The first class can run 4-point or 2-point tiles; for FP32 hierarchies the autotuner covers,
+// both tilings of that class are timed on the zeroed batch arenas (3 interleaved rounds of a
+// warm-up and 2 launches, minimum kept; CHFPE_STAGE_VARIANT=0 or 3 forces 2 or 4 points) and
+// the faster is kept.  The 2-point and 1-point classes have one tiling each.
 template <typename T>
 static chfpe_status batch_setup_geo(chfpe_handle *b) {
     const int n = (int)b->inst.size();
     std::vector<InstGeo<T>> geo(n);
-    std::vector<int2> wv, ws;
+    std::vector<int2> w4, w4as2, w2, w1;
     for (int i = 0; i < n; ++i) {
         geo[i].g = geo_of<T>(b->inst[i]);
         geo[i].off = b->inst_off[i];
         const chfpe_handle *c = b->inst[i];
-        const bool vec = c->n[2 * c->d - 1] % kVec == 0;
-        const int per_tile = 128 * (vec ? kVec : 1);
-        const int tiles = (c->P + per_tile - 1) / per_tile;
-        for (int t = 0; t < tiles; ++t) (vec ? wv : ws).push_back(make_int2(i, t));
+        const int npd = c->n[2 * c->d - 1];
+        auto tiles = [&](int per_tile, std::vector<int2> &w) {
+            for (int t = 0; t < (c->P + per_tile - 1) / per_tile; ++t) w.push_back(make_int2(i, t));
+        };
+        if (npd % 4 == 0) { tiles(512, w4); tiles(256, w4as2); }
+        else if (npd % 2 == 0) tiles(256, w2);
+        else tiles(128, w1);
     }
     chfpe_status st = CHFPE_OK;
     b->d_geo = dalloc<InstGeo<T>>(n, &st);
-    if (!wv.empty()) b->d_work_vec = dalloc<int2>(wv.size(), &st);
-    if (!ws.empty()) b->d_work_sc = dalloc<int2>(ws.size(), &st);
     if (st) return st;
-    b->nwork_vec = (int)wv.size();
-    b->nwork_sc = (int)ws.size();
     CK(cudaMemcpyAsync(b->d_geo, geo.data(), n * sizeof(InstGeo<T>), cudaMemcpyHostToDevice, b->stream));
-    if (!wv.empty())
-        CK(cudaMemcpyAsync(b->d_work_vec, wv.data(), wv.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
-    if (!ws.empty())
-        CK(cudaMemcpyAsync(b->d_work_sc, ws.data(), ws.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    for (double &u : b->tune_us) u = -1.0;
+    b->variant = 0;
+    bool four = sizeof(T) == 4 && tunable(4, b->d, b->depth) && !w4.empty();
+    const char *env = getenv("CHFPE_STAGE_VARIANT");
+    if (four && env && env[0]) {
+        four = atoi(env) == 3;
+    } else if (four) {
+        // time the class on its own: 4-point tiles (list 0) against 2-point tiles (list 1)
+        size_t bytes = 0;
+        for (chfpe_handle *c : b->inst) bytes += (size_t)c->state_bytes;
+        CK(cudaMemsetAsync(b->ca, 0, bytes, b->stream));
+        CK(cudaMemsetAsync(b->cb, 0, bytes, b->stream));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(CHFPE_ECUDA, "event create"); }
+        cudaError_t e = cudaSuccess;
+        double us[2] = {1e30, 1e30};
+        for (int round = 0; round < 3 && e == cudaSuccess; ++round)
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                if ((st = set_work(b, 0, k == 0 ? w4 : std::vector<int2>()))) break;
+                if ((st = set_work(b, 1, k == 1 ? w4as2 : std::vector<int2>()))) break;
+                if ((st = set_work(b, 2, std::vector<int2>()))) break;
+                if ((st = batch_stage<T>(b, b->ca, b->cb, b->cb, 1e-3))) break;   // warm-up
+                e = cudaEventRecord(e0, b->stream);
+                for (int r = 0; r < 2 && e == cudaSuccess && !st; ++r) st = batch_stage<T>(b, b->ca, b->cb, b->cb, 1e-3);
+                if (st) break;
+                if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess) us[k] = std::min(us[k], 1e3 * ms / 2.0);
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st) return st;
+        if (e != cudaSuccess) return fail(CHFPE_ECUDA, std::string("batch autotune: ") + cudaGetErrorString(e));
+        b->tune_us[3] = us[0];
+        b->tune_us[0] = us[1];
+        four = us[0] <= us[1];
+        b->launches = 0;
+    }
+    if (four) b->variant = 3;
+    std::vector<int2> l2 = w2;
+    if (!four) l2.insert(l2.end(), w4as2.begin(), w4as2.end());
+    if ((st = set_work(b, 0, four ? w4 : std::vector<int2>()))) return st;
+    if ((st = set_work(b, 1, l2))) return st;
+    if ((st = set_work(b, 2, w1))) return st;
     CK(cudaStreamSynchronize(b->stream));
     return CHFPE_OK;
 }

@@ -9,7 +9,7 @@ Training and inference run in libchfpe's surrogate kernels (``chfpe.Surrogate``)
 only marshals arrays, schedules the learning rate, and routes parameter vectors outside the
 training ranges to the solver (the fallback).
 
-    python -m paper_2509_25840_b300.surrogate --n-train 2048 --n-test 256 --epochs 200
+    python -m paper_2509_25840_b300.surrogate --n-train 1024 --n-test 256 --data surr_data.npz
 """
 from __future__ import annotations
 
@@ -187,14 +187,14 @@ def inference_rate(sur: "chfpe.Surrogate", n: int = 4096, reps: int = 5) -> floa
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--n-train", type=int, default=2048)
+    ap.add_argument("--n-train", type=int, default=1024)
     ap.add_argument("--n-test", type=int, default=256)
-    ap.add_argument("--n-axis", type=int, default=16)
+    ap.add_argument("--n-axis", type=int, default=10)
     ap.add_argument("--depth", type=int, default=2)
-    ap.add_argument("--epochs", type=int, default=200)
-    ap.add_argument("--batch", type=int, default=256)
-    ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--wd", type=float, default=1e-4, help="AdamW decoupled weight decay")
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--wd", type=float, default=1e-2, help="AdamW decoupled weight decay")
     ap.add_argument("--w-scale", type=float, default=0.1, help="weight of the log-scale loss")
     ap.add_argument("--data", default=None, help="npz cache of the solver data (read if present)")
     ap.add_argument("--seed0", type=int, default=100000)

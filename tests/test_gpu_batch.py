@@ -136,3 +136,29 @@ def test_bf16_deep_tiers_error_vs_fp64(batch):
     print(f"bf16 tiers: normalised R1 error vs FP64 oracle {err[3]:.2e} (plain FP32 {err[0]:.2e})")
     assert err[0] < 1e-4
     assert err[3] < 1e-4
+
+
+def test_batch_tilings_of_the_multiple_of_4_class_agree(monkeypatch):
+    """Instances whose p_2 extent is a multiple of 4 run 4-point or 2-point tiles (chosen by the
+    autotuner, forced here); both against single handles, FP32."""
+    chfpe = _chfpe()
+    insts = _instances()           # p_2 extents 10, 13 (2-point and 1-point classes) and 12
+    depth, dt, nt, stride = 2, 0.004, 5, 4
+    mu = inputs.Optical(lin=(1.0, 1.0), quad=[[0.2, 0.0], [0.0, -0.1]])
+    out = {}
+    for forced in ("0", "3"):
+        monkeypatch.setenv("CHFPE_STAGE_VARIANT", forced)
+        with chfpe.Batch([m for m, _ in insts], [g for _, g in insts], depth=depth, dt=dt,
+                         precision=32) as b:
+            assert b.stage_tuning()[0] == int(forced)
+            for i, (m, g) in enumerate(insts):
+                b.instance(i).set_equilibrium(_eq(m, g, depth))
+            out[forced] = b.response1_all(mu, mu, nt, stride)
+    monkeypatch.delenv("CHFPE_STAGE_VARIANT")
+    with chfpe.Batch([m for m, _ in insts], [g for _, g in insts], depth=depth, dt=dt,
+                     precision=32) as b:
+        v, us = b.stage_tuning()
+    assert v in (0, 3) and us[0] > 0 and us[3] > 0 and us[v] == min(us[0], us[3])
+    for i in range(len(insts)):
+        scale = np.abs(out["0"][i]).max()
+        assert np.abs(out["0"][i] - out["3"][i]).max() <= 1e-6 * scale
