@@ -260,6 +260,19 @@ chfpe_status chfpe_surrogate_gemm(const void *A, int ta, int lda, const void *B,
                                   float *C, const float *bias, int M, int N, int K, int splits,
                                   void *stream);
 
+/* ---- persistent propagation (no counterpart in the paper) -------------------------------------
+ *
+ * For small problems (batch x cells <= 4e6; (modes, depth) = (1, 5), (2, 2), (2, 4); plain
+ * storage) the sampled propagations of chfpe_response1 and of chfpe_response2's branch phase run
+ * as ONE cooperative launch: the RK4 stages and the FP64 observable reduction are separated by
+ * grid-wide barriers instead of kernel boundaries (the launch gaps dominate there).  The results
+ * equal the launch-per-stage path's up to the order of the reduction's additions.  Every barrier
+ * wait is bounded (1 s); a wait that gives up makes the call return CHFPE_ETIMEOUT and leaves the
+ * handle usable.  CHFPE_PERSISTENT=0 in the environment disables the path (it is also off while
+ * chfpe_stats_reset(h, 1) timing is on); CHFPE_TEST_PRESET_ERROR=1 sets the error word before
+ * each persistent launch, to exercise that error path in tests.
+ */
+
 /* ---- stage-kernel autotuning (no counterpart in the paper) ----------------------------------
  *
  * The RK4 stage kernel has CHFPE_STAGE_VARIANTS launch shapes (points per thread, threads per

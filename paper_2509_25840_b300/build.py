@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libchfpe.so")
 SOURCES = [os.path.join(HERE, "csrc", f) for f in ("chfpe.cu", "noalloc.cu", "surrogate.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("kernels.cuh", "bulk.cuh")] + [os.path.join(ROOT, "include", "chfpe.h")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("kernels.cuh", "bulk.cuh", "persistent.cuh")] + [os.path.join(ROOT, "include", "chfpe.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 

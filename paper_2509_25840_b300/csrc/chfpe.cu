@@ -4,6 +4,7 @@
 #include "../../include/chfpe.h"
 #include "kernels.cuh"
 #include "bulk.cuh"
+#include "persistent.cuh"
 
 #include <cuda_runtime.h>
 
@@ -91,7 +92,9 @@ struct chfpe_handle {
     double stage_bytes = 0.0, cell_updates = 0.0;
     bool time_stages = false;
     bool force_scalar = false;          // CHFPE_SCALAR_STAGE=1: one point per thread (V = 1)
-    int *d_err = nullptr;               // device error word of the bounded waits (bulk stage)
+    int *d_err = nullptr;               // device error word of the bounded waits (bulk, persistent)
+    unsigned *d_bar = nullptr;          // grid barrier of the persistent kernel: arrivals, generation
+    int use_persistent = 1;             // CHFPE_PERSISTENT=0 disables the persistent propagation
     int variant = 0;                    // stage launch shape (kStageVariants), set by autotune()
     double tune_us[CHFPE_STAGE_VARIANTS] = {};   // measured us per launch, -1 = not available
     std::vector<cudaEvent_t> ev;        // pairs (start, stop) of timed bursts
@@ -659,7 +662,7 @@ extern "C" void chfpe_destroy(chfpe_handle *h) {
     if (h->borrowed_arenas) h->cy = h->ca = h->cb = h->eq = nullptr;
     void *ptrs[] = {h->U_d, h->F_d, h->F_f, h->wp, h->CWq, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
                     h->cy, h->ca, h->cb, h->by, h->ba, h->bb, h->eq, h->stage64, h->partial, h->dR,
-                    h->counter, h->d_err, h->d_geo, h->d_work[0], h->d_work[1], h->d_work[2]};
+                    h->counter, h->d_err, h->d_bar, h->d_geo, h->d_work[0], h->d_work[1], h->d_work[2]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -753,9 +756,12 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
     h->partial = dalloc<double>(h->partial_cap, &st);
     h->counter = dalloc<int>(1, &st);
     h->d_err = dalloc<int>(1, &st);
+    h->d_bar = dalloc<unsigned>(2, &st);
     {
         const char *eg = getenv("CHFPE_GRAPHS");
         if (eg) h->use_graphs = atoi(eg);
+        const char *ep = getenv("CHFPE_PERSISTENT");
+        if (ep && ep[0] == '0') h->use_persistent = 0;
     }
     (void)sb;
     const size_t sbytes = (size_t)h->state_bytes;
@@ -1081,10 +1087,116 @@ static chfpe_status finish_response(chfpe_handle *h, double *R, size_t n) {
 // When the states are small enough that launch overhead matters, one interval (the stride RK4
 // steps followed by the observation) is captured once as a CUDA graph and replayed, the output
 // slot advancing through a device-side counter.
+// ------------------------------------------------------------------------------------------
+// persistent propagation (persistent.cuh): one cooperative launch for a whole sampled
+// propagation of small states, where stages take microseconds and launch gaps dominate
+// ------------------------------------------------------------------------------------------
+
+constexpr double kPersistCells = 4.0e6;   // batch x cells up to which the persistent path is used
+
+static bool persistent_config(int d, int depth) {
+    return (d == 1 && depth == 5) || (d == 2 && (depth == 2 || depth == 4));
+}
+
+template <typename T, int D, int DEPTH, int V, int NT>
+static chfpe_status launch_persistent(chfpe_handle *h, PersistArgs p) {
+    auto kern = persistent_kernel<T, D, DEPTH, V, NT>;
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return fail(CHFPE_ECUDA, "cooperative launch not supported");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0));
+    p.tiles_per_state = (int)((h->P + (long long)NT * V - 1) / ((long long)NT * V));
+    const long long tiles = (long long)p.tiles_per_state * p.batch;
+    const long long grid = std::min<long long>(tiles, (long long)per_sm * sms);
+    if (grid < 1) return fail(CHFPE_EINVAL, "persistent propagation: no co-resident blocks");
+    CK(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
+    {   // test hook: the error word set before the launch, as if a wait had given up
+        const char *ef = getenv("CHFPE_TEST_PRESET_ERROR");
+        if (ef && ef[0] == '1') {
+            const int one = 1;
+            CK(cudaMemcpyAsync(h->d_err, &one, sizeof one, cudaMemcpyHostToDevice, h->stream));
+        }
+    }
+    Geo<T> g = geo_of<T>(h);
+    void *args[] = {&g, &p};
+    CK(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid), dim3(NT), args, 0, h->stream));
+    ++h->launches;
+    return CHFPE_OK;
+}
+
+// Tile shapes of the persistent kernel, (threads, points per thread): (128, 2), (32, 2), (32, 1).
+// The first that gives every SM at least one tile of ONE state is used (small states spread over
+// the whole GPU -- their FP64 stages are compute-bound per SM); with none, the one with the most
+// tiles.  The choice does not depend on the batch, so results do not depend on the chunking of
+// R2's branches.
+template <typename T>
+static chfpe_status persistent_dispatch(chfpe_handle *h, const PersistArgs &p, bool vec) {
+    int dev = 0, sms = 148;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const double pts = (double)h->P;
+    const int shape = (vec && pts / 256.0 >= sms) ? 0 : (vec && pts / 64.0 >= sms) ? 1 : 2;
+#define PCASE(D_, K_)                                                                 \
+    if (h->d == D_ && h->depth == K_) {                                               \
+        if (shape == 0) return launch_persistent<T, D_, K_, 2, 128>(h, p);            \
+        if (shape == 1) return launch_persistent<T, D_, K_, 2, 32>(h, p);             \
+        return launch_persistent<T, D_, K_, 1, 32>(h, p);                             \
+    }
+    PCASE(1, 5)
+    PCASE(2, 2)
+    PCASE(2, 4)
+#undef PCASE
+    return fail(CHFPE_EINVAL, "persistent propagation: configuration not compiled");
+}
+
+static bool persistent_ok(const chfpe_handle *h, int batch, int nsamples) {
+    const long long chunks = (h->P + kObsChunk - 1) / kObsChunk;   // partial sums per state
+    return h->use_persistent && !h->time_stages && h->M32 == h->M && nsamples >= 2 &&
+           persistent_config(h->d, h->depth) && (double)batch * (double)h->state <= kPersistCells &&
+           chunks * batch <= h->partial_cap;
+}
+
+static chfpe_status persistent_propagation(chfpe_handle *h, void *y, void *za, void *zb, int batch,
+                                           int nsamples, int stride, double *out,
+                                           long long out_stride) {
+    PersistArgs p;
+    memset(&p, 0, sizeof(p));
+    p.y = (char *)y;
+    p.za = (char *)za;
+    p.zb = (char *)zb;
+    p.state_bytes = h->state_bytes;
+    p.batch = batch;
+    p.dt = h->dt;
+    p.nsamples = nsamples;
+    p.stride = stride;
+    p.CWq = h->CWq;
+    p.wp = h->wp;
+    p.wp_ld = h->wp_ld;
+    double vol = 1.0;
+    for (int ax = 0; ax < 2 * h->d; ++ax) vol *= h->h[ax];
+    p.vol = vol;
+    p.partial = h->partial;
+    p.out = out;
+    p.out_stride = out_stride;
+    p.bar = h->d_bar;
+    p.err = h->d_err;
+    const bool vec = (h->n[2 * h->d - 1] % kVec == 0) && aligned16(y) && aligned16(za) &&
+                     aligned16(zb) && !h->force_scalar;
+    chfpe_status st = h->prec == 64 ? persistent_dispatch<double>(h, p, vec)
+                                    : persistent_dispatch<float>(h, p, vec);
+    if (st) return st;
+    h->cell_updates += (double)batch * (double)h->state * (double)stride * (double)(nsamples - 1);
+    return CHFPE_OK;
+}
+
 static chfpe_status sampled_propagation(chfpe_handle *h, void *y, void *za, void *zb, int batch,
                                         int nsamples, int stride, double *out,
                                         long long out_stride) {
     chfpe_status st;
+    if (persistent_ok(h, batch, nsamples))
+        return persistent_propagation(h, y, za, zb, batch, nsamples, stride, out, out_stride);
     const double cells = (double)batch * (double)h->state;
     bool graphs = h->use_graphs == 1 || (h->use_graphs < 0 && cells * (4.0 * stride) < 2e9 &&
                                          stride > 0 && nsamples > 2 && !h->time_stages);

@@ -119,18 +119,6 @@ struct StageArgs {
     Geo<T> g;
 };
 
-template <typename T>
-__device__ __forceinline__ T stencil7(const T *__restrict__ f, int x, int i, int N, int st) {
-    // (45 (f+1 - f-1) - 9 (f+2 - f-2) + (f+3 - f-3)), zero outside [0, N)
-    T p1 = (i + 1 < N) ? __ldg(f + x + st) : T(0);
-    T m1 = (i >= 1) ? __ldg(f + x - st) : T(0);
-    T p2 = (i + 2 < N) ? __ldg(f + x + 2 * st) : T(0);
-    T m2 = (i >= 2) ? __ldg(f + x - 2 * st) : T(0);
-    T p3 = (i + 3 < N) ? __ldg(f + x + 3 * st) : T(0);
-    T m3 = (i >= 3) ? __ldg(f + x - 3 * st) : T(0);
-    return T(45) * (p1 - m1) - T(9) * (p2 - m2) + (p3 - m3);
-}
-
 // ------------------------------------------------------------------------------------------
 // vector loads / stores of V consecutive values, stored as T or as bf16
 // ------------------------------------------------------------------------------------------
@@ -146,11 +134,14 @@ template <> struct BfVecOf<1> { typedef unsigned short type; };
 template <> struct BfVecOf<2> { typedef unsigned int type; };
 template <> struct BfVecOf<4> { typedef uint2 type; };
 
-template <typename T, int V>
+// NC = true reads through the non-coherent path (data read-only for the kernel's lifetime);
+// NC = false reads through L2 only (ld.global.cg, coherent across SMs), for kernels that rewrite
+// the state between grid barriers
+template <typename T, int V, bool NC = true>
 __device__ __forceinline__ void vload(const T *__restrict__ p, bool ok, T (&v)[V]) {
     typedef typename VecOf<T, V>::type VT;
     if (ok) {
-        const VT u = __ldg(reinterpret_cast<const VT *>(p));
+        const VT u = NC ? __ldg(reinterpret_cast<const VT *>(p)) : __ldcg(reinterpret_cast<const VT *>(p));
         const T *e = reinterpret_cast<const T *>(&u);
 #pragma unroll
         for (int j = 0; j < V; ++j) v[j] = e[j];
@@ -160,11 +151,11 @@ __device__ __forceinline__ void vload(const T *__restrict__ p, bool ok, T (&v)[V
     }
 }
 
-template <typename T, int V>
+template <typename T, int V, bool NC = true>
 __device__ __forceinline__ void vload(const bf16 *__restrict__ p, bool ok, T (&v)[V]) {
     typedef typename BfVecOf<V>::type VT;
     if (ok) {
-        const VT u = __ldg(reinterpret_cast<const VT *>(p));
+        const VT u = NC ? __ldg(reinterpret_cast<const VT *>(p)) : __ldcg(reinterpret_cast<const VT *>(p));
         const bf16 *e = reinterpret_cast<const bf16 *>(&u);
 #pragma unroll
         for (int j = 0; j < V; ++j) v[j] = (T)__bfloat162float(e[j]);
@@ -214,16 +205,16 @@ __device__ __forceinline__ void vstore(bf16 *p, const T (&v)[V]) {
 }
 
 // (45 (f+1 - f-1) - 9 (f+2 - f-2) + (f+3 - f-3)) along a non-fastest axis, V points at once
-template <typename S, typename T, int V>
+template <typename S, typename T, int V, bool NC = true>
 __device__ __forceinline__ void vstencil(const S *__restrict__ f, int x0, int i, int N, int st,
                                          T (&out)[V]) {
     T p1[V], m1[V], p2[V], m2[V], p3[V], m3[V];
-    vload<T, V>(f + x0 + st, i + 1 < N, p1);
-    vload<T, V>(f + x0 - st, i >= 1, m1);
-    vload<T, V>(f + x0 + 2 * st, i + 2 < N, p2);
-    vload<T, V>(f + x0 - 2 * st, i >= 2, m2);
-    vload<T, V>(f + x0 + 3 * st, i + 3 < N, p3);
-    vload<T, V>(f + x0 - 3 * st, i >= 3, m3);
+    vload<T, V, NC>(f + x0 + st, i + 1 < N, p1);
+    vload<T, V, NC>(f + x0 - st, i >= 1, m1);
+    vload<T, V, NC>(f + x0 + 2 * st, i + 2 < N, p2);
+    vload<T, V, NC>(f + x0 - 2 * st, i >= 2, m2);
+    vload<T, V, NC>(f + x0 + 3 * st, i + 3 < N, p3);
+    vload<T, V, NC>(f + x0 - 3 * st, i >= 3, m3);
 #pragma unroll
     for (int j = 0; j < V; ++j)
         out[j] = T(45) * (p1[j] - m1[j]) - T(9) * (p2[j] - m2[j]) + (p3[j] - m3[j]);
@@ -243,7 +234,7 @@ __device__ __forceinline__ const bf16 *member_h(const char *base, int m, int P) 
 // one member at V points: its own Liouvillian terms k = sum_s [F_s D_ps g - v_s D_qs g] (the
 // q-derivatives are consumed at once), its p-derivatives dp_s (kept for the hierarchy links) and
 // its values; the p_d derivative comes from a window of (2 NS + 1) vectors
-template <typename S, typename T, int D, int V>
+template <typename S, typename T, int D, int V, bool NC = true>
 __device__ __forceinline__ void member_terms(const S *__restrict__ g, const Geo<T> &a, int x0,
                                              const int (&idx)[2 * D], const T (&Fs)[D],
                                              const T (&vq)[D][V], T (&k)[V], T (&dp)[D][V],
@@ -257,7 +248,7 @@ __device__ __forceinline__ void member_terms(const S *__restrict__ g, const Geo<
     for (int b = 0; b < 2 * NS + 1; ++b) {
         const int off = (b - NS) * V;
         T tmp[V];
-        vload<T, V>(g + x0 + off, iL + off >= 0 && iL + off < NL, tmp);
+        vload<T, V, NC>(g + x0 + off, iL + off >= 0 && iL + off < NL, tmp);
 #pragma unroll
         for (int j = 0; j < V; ++j) w[b * V + j] = tmp[j];
     }
@@ -266,9 +257,9 @@ __device__ __forceinline__ void member_terms(const S *__restrict__ g, const Geo<
 #pragma unroll
     for (int s = 0; s < D; ++s) {
         T dq[V];
-        vstencil<S, T, V>(g, x0, idx[s], a.n[s], a.st[s], dq);
+        vstencil<S, T, V, NC>(g, x0, idx[s], a.n[s], a.st[s], dq);
         if (s < D - 1) {
-            vstencil<S, T, V>(g, x0, idx[D + s], a.n[D + s], a.st[D + s], dp[s]);
+            vstencil<S, T, V, NC>(g, x0, idx[D + s], a.n[D + s], a.st[D + s], dp[s]);
         } else {
 #pragma unroll
             for (int j = 0; j < V; ++j) {
@@ -295,7 +286,7 @@ __device__ __forceinline__ void member_terms(const S *__restrict__ g, const Geo<
 // window of (2 NS + 1) vectors, NS = ceil(3 / V).
 // ------------------------------------------------------------------------------------------
 
-template <typename T, int D, int DEPTH, int V, int M32>
+template <typename T, int D, int DEPTH, int V, int M32, bool NC = true>
 __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, const char *y,
                                              char *out, T c, int x0) {
     constexpr MemberTable<D, DEPTH> tab{};
@@ -339,9 +330,9 @@ __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, co
     for (int m = 0; m < M; ++m) {
         T k[V], dp[D][V], v[V];
         if (m < M32)
-            member_terms<T, T, D, V>(member_t<T, M32>(in, m, a.P), a, x0, idx, Fs, vq, k, dp, v);
+            member_terms<T, T, D, V, NC>(member_t<T, M32>(in, m, a.P), a, x0, idx, Fs, vq, k, dp, v);
         else
-            member_terms<bf16, T, D, V>(member_h<T, M32>(in, m, a.P), a, x0, idx, Fs, vq, k, dp, v);
+            member_terms<bf16, T, D, V, NC>(member_h<T, M32>(in, m, a.P), a, x0, idx, Fs, vq, k, dp, v);
         T gm = T(0);
 #pragma unroll
         for (int s = 0; s < D; ++s) gm += T(tab.n[m][s]) * a.gam[s];

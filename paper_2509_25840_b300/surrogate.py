@@ -197,6 +197,10 @@ def main(argv=None):
     ap.add_argument("--wd", type=float, default=1e-2, help="AdamW decoupled weight decay")
     ap.add_argument("--w-scale", type=float, default=0.1, help="weight of the log-scale loss")
     ap.add_argument("--data", default=None, help="npz cache of the solver data (read if present)")
+    ap.add_argument("--extra-data", default=None,
+                    help="further npz files (comma-separated) appended to the training set only")
+    ap.add_argument("--generate-only", action="store_true",
+                    help="solve and save the n-train + n-test spectra to --data, no training")
     ap.add_argument("--seed0", type=int, default=100000)
     args = ap.parse_args(argv)
     chfpe.load()
@@ -211,8 +215,17 @@ def main(argv=None):
         n_solved = n_all
         if args.data:
             np.savez(args.data, X=X, R=R.astype(np.float32), t_solve=t_solve, n_solved=n_solved)
+    if args.generate_only:
+        print(json.dumps({"generated": int(n_solved), "seconds": t_solve, "data": args.data}))
+        return None
     Xtr, Rtr = X[:args.n_train], R[:args.n_train]
     Xte, Rte = X[args.n_train:n_all], R[args.n_train:n_all]
+    for extra in filter(None, (args.extra_data or "").split(",")):
+        d = np.load(extra)
+        Xtr = np.concatenate([Xtr, d["X"]])
+        Rtr = np.concatenate([Rtr, d["R"].astype(np.float64)])
+        t_solve += float(d["t_solve"])
+        n_solved += int(d["n_solved"])
     torch = _torch()
     with make_surrogate(max_batch=max(args.batch, 256), seed=1) as sur:
         t0 = time.perf_counter()

@@ -312,3 +312,51 @@ def test_autotuner_times_the_shapes_and_keeps_the_fastest(monkeypatch):
     with chfpe.Handle(model, grid, depth=4, dt=0.004, precision=64) as h:   # not tuned
         v, us = h.stage_tuning()
     assert v == 0 and np.all(us == -1)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_persistent_propagation_matches_launch_per_stage(prec, monkeypatch):
+    """The one-launch persistent R1 (grid barriers between stages, in-kernel reduction) against
+    the launch-per-stage path on the one-mode workload and a small two-mode case."""
+    chfpe = _chfpe()
+    wl = inputs.one_mode_64(nt=201, stride=2)
+    W = ref.hierarchy_state(ref.boltzmann_sym(wl.model, wl.grid), inputs.member_count(1, wl.depth))
+    m2 = _model(2)
+    g2 = inputs.default_grid(m2, [9, 11, 12, 16], cut=12.0, nsigma=5.0)
+    W2 = ref.hierarchy_state(ref.boltzmann_sym(m2, g2), inputs.member_count(2, 4))
+    mu2 = inputs.Optical(lin=(1.0, 0.5), quad=[[0.2, 0.1], [0.0, -0.1]])
+    for model, grid, depth, dt, Weq, A, C, nt, stride in (
+            (wl.model, wl.grid, wl.depth, wl.dt, W, wl.A, wl.C, 201, 2),
+            (m2, g2, 4, 0.004, W2, mu2, mu2, 12, 5)):
+        got = {}
+        for persistent in ("1", "0"):
+            monkeypatch.setenv("CHFPE_PERSISTENT", persistent)
+            with chfpe.Handle(model, grid, depth=depth, dt=dt, precision=prec) as h:
+                h.set_equilibrium(Weq)
+                got[persistent] = h.response1(A, C, nt, stride)
+                launches = h.stats()["kernel_launches"]
+            if persistent == "1":
+                assert launches < 20             # set-up, insertion, one persistent launch
+        scale = np.abs(got["0"]).max()
+        tol = 1e-12 if prec == 64 else 1e-6
+        assert np.abs(got["1"] - got["0"]).max() <= tol * scale
+
+
+def test_persistent_barrier_error_reports_timeout_and_recovers(monkeypatch):
+    """The grid barrier's error path: with the error word set before the launch (as if a wait had
+    given up) every block leaves at its first barrier, the call returns CHFPE_ETIMEOUT, and the
+    next call on the same handle runs normally."""
+    chfpe = _chfpe()
+    wl = inputs.one_mode_64(nt=21, stride=2)
+    W = ref.hierarchy_state(ref.boltzmann_sym(wl.model, wl.grid), inputs.member_count(1, wl.depth))
+    monkeypatch.setenv("CHFPE_PERSISTENT", "1")
+    with chfpe.Handle(wl.model, wl.grid, depth=wl.depth, dt=wl.dt, precision=64) as h:
+        h.set_equilibrium(W)
+        want = h.response1(wl.A, wl.C, 21, 2)
+        monkeypatch.setenv("CHFPE_TEST_PRESET_ERROR", "1")
+        with pytest.raises(chfpe.ChfpeError) as e:
+            h.response1(wl.A, wl.C, 21, 2)
+        assert e.value.status == chfpe.ETIMEOUT
+        monkeypatch.delenv("CHFPE_TEST_PRESET_ERROR")
+        again = h.response1(wl.A, wl.C, 21, 2)
+    np.testing.assert_array_equal(again, want)
