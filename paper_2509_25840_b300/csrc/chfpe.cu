@@ -176,6 +176,8 @@ static int bf16_m32(int d, int depth, int tier) {
 //   4  shape 3 with every member's tile staged in shared memory by bulk async copies, double
 //      buffered across members (two modes only; bulk.cuh)
 //   5  shape 4 with the buffers filled by every thread's 16-byte cp.async copies
+//   6  shape 3 with 256 threads (2 blocks per SM)
+//   7  shape 3 with 64 threads (8 blocks per SM)
 constexpr bool tunable(int T_size, int D, int DEPTH) {
     return T_size == 4 && ((D == 1 && DEPTH == 5) || (D == 2 && (DEPTH == 2 || DEPTH == 4)) ||
                            (D == 3 && DEPTH == 2));
@@ -229,6 +231,8 @@ static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int varia
         case 1: launch_vec<T, D, DEPTH, M32, 2, 256, MINB / 2>(a, batch, s); return;
         case 2: launch_vec<T, D, DEPTH, M32, 2, 128, 6>(a, batch, s); return;
         case 3: launch_vec<T, D, DEPTH, M32, 4, 128, 4>(a, batch, s); return;
+        case 6: launch_vec<T, D, DEPTH, M32, 4, 256, 2>(a, batch, s); return;
+        case 7: launch_vec<T, D, DEPTH, M32, 4, 64, 8>(a, batch, s); return;
         case 4:
         case 5:
             if constexpr (D == 2) {
@@ -275,7 +279,7 @@ static bool launch_stage(const chfpe_handle *h, const StageArgs<T> &a, int batch
     cudaStream_t s = h->stream;
     const bool vec = (h->n[2 * h->d - 1] % kVec == 0) && aligned16(a.in) && aligned16(a.y) &&
                      aligned16(a.out) && !h->force_scalar;
-    // shapes 3 and 4 read 4 consecutive p_d points: only where rows hold whole groups of 4
+    // shapes 3-7 read 4 consecutive p_d points: only where rows hold whole groups of 4
     const int variant = (h->variant >= 3 && h->n[2 * h->d - 1] % 4 != 0) ? 0 : h->variant;
 #define CASE(D_, K_) \
     case (D_ * 16 + K_): return launch_stage_t<T, D_, K_>(a, batch, vec, m32, variant, h->d_err, s);
@@ -836,7 +840,7 @@ static chfpe_status autotune(chfpe_handle *h) {
     for (int round = 0; round < 3 && e == cudaSuccess; ++round) {
         for (int v = 0; v < CHFPE_STAGE_VARIANTS && e == cudaSuccess; ++v) {
             if (v >= 3 && npd % 4 != 0) continue;
-            if (v >= 4 && h->d != 2) continue;
+            if ((v == 4 || v == 5) && h->d != 2) continue;
             if (round > 0 && h->tune_us[v] < 0) continue;   // disqualified in an earlier round
             h->variant = v;
             launch_stage<float>(h, a, batch);   // warm-up
