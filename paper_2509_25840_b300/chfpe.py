@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libchfpe.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
-STAGE_VARIANTS = 8
+STAGE_VARIANTS = 9
 _NAMES = {0: "CHFPE_OK", 1: "CHFPE_EINVAL", 2: "CHFPE_ENOMEM", 3: "CHFPE_ECUDA",
           4: "CHFPE_EUNSTABLE", 5: "CHFPE_ETIMEOUT", 6: "CHFPE_ESTATE"}
 
@@ -50,7 +50,8 @@ class chfpe_grid(ctypes.Structure):
 
 class chfpe_options(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int), ("precision", ctypes.c_int), ("dt", ctypes.c_double),
-                ("max_batch", ctypes.c_int), ("stream", ctypes.c_void_p), ("bf16_tier", ctypes.c_int)]
+                ("max_batch", ctypes.c_int), ("stream", ctypes.c_void_p), ("bf16_tier", ctypes.c_int),
+                ("truncation", ctypes.c_int)]
 
 
 class chfpe_stats(ctypes.Structure):

@@ -178,15 +178,16 @@ static int bf16_m32(int d, int depth, int tier) {
 //   5  shape 4 with the buffers filled by every thread's 16-byte cp.async copies
 //   6  shape 3 with 256 threads (2 blocks per SM)
 //   7  shape 3 with 64 threads (8 blocks per SM)
+//   8  shape 3 with L1 prefetch hints for the next member's q-neighbours
 constexpr bool tunable(int T_size, int D, int DEPTH) {
     return T_size == 4 && ((D == 1 && DEPTH == 5) || (D == 2 && (DEPTH == 2 || DEPTH == 4)) ||
                            (D == 3 && DEPTH == 2));
 }
 
-template <typename T, int D, int DEPTH, int M32, int V, int NT, int MINB>
+template <typename T, int D, int DEPTH, int M32, int V, int NT, int MINB, bool PF = false>
 static void launch_vec(const StageArgs<T> &a, int batch, cudaStream_t s) {
     const int nthr = a.g.P / V;
-    stage_vec_kernel<T, D, DEPTH, V, NT, MINB, M32><<<dim3((nthr + NT - 1) / NT, batch), NT, 0, s>>>(a);
+    stage_vec_kernel<T, D, DEPTH, V, NT, MINB, M32, PF><<<dim3((nthr + NT - 1) / NT, batch), NT, 0, s>>>(a);
 }
 
 constexpr int kBulkNT = 128, kBulkTP = kBulkNT * 4;
@@ -233,6 +234,7 @@ static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int varia
         case 3: launch_vec<T, D, DEPTH, M32, 4, 128, 4>(a, batch, s); return;
         case 6: launch_vec<T, D, DEPTH, M32, 4, 256, 2>(a, batch, s); return;
         case 7: launch_vec<T, D, DEPTH, M32, 4, 64, 8>(a, batch, s); return;
+        case 8: launch_vec<T, D, DEPTH, M32, 4, 128, 4, true>(a, batch, s); return;
         case 4:
         case 5:
             if constexpr (D == 2) {
@@ -637,6 +639,8 @@ static chfpe_status validate(const chfpe_model *m, const chfpe_grid *g, const ch
     if (o->depth < 0 || o->depth > max_depth_for(m->nmodes))
         return fail(CHFPE_EINVAL, "depth out of range (d=1: <=8, d=2: <=5, d=3: <=3)");
     if (o->precision != 32 && o->precision != 64) return fail(CHFPE_EINVAL, "precision must be 32 or 64");
+    if (o->truncation != 0)
+        return fail(CHFPE_EINVAL, "truncation: only 0 (n_1 + .. + n_d <= depth) is built");
     if (!(o->dt > 0) || !is_fin(o->dt)) return fail(CHFPE_EINVAL, "dt must be positive");
     if (o->max_batch < 0 || o->max_batch > 65535) return fail(CHFPE_EINVAL, "max_batch must be in 0..65535");
     long long P = 1;

@@ -275,6 +275,24 @@ __device__ __forceinline__ void member_terms(const S *__restrict__ g, const Geo<
     for (int j = 0; j < V; ++j) v[j] = w[NS * V + j];
 }
 
+// L1 prefetch hint for one member's stencil neighbours along the q axes (in-bounds addresses
+// only; the neighbours that miss L1): issued for member m + 1 while member m is computed
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+template <typename S, typename T, int D>
+__device__ __forceinline__ void prefetch_member(const S *g, const Geo<T> &a, int x0,
+                                                const int (&idx)[2 * D]) {
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax)
+#pragma unroll
+        for (int k = 1; k <= 3; ++k) {
+            if (idx[ax] + k < a.n[ax]) prefetch_l1(g + x0 + k * a.st[ax]);
+            if (idx[ax] >= k) prefetch_l1(g + x0 - k * a.st[ax]);
+        }
+}
+
 // ------------------------------------------------------------------------------------------
 // fused RHS + RK4 stage for V consecutive p_d points of one state
 //
@@ -286,7 +304,7 @@ __device__ __forceinline__ void member_terms(const S *__restrict__ g, const Geo<
 // window of (2 NS + 1) vectors, NS = ceil(3 / V).
 // ------------------------------------------------------------------------------------------
 
-template <typename T, int D, int DEPTH, int V, int M32, bool NC = true>
+template <typename T, int D, int DEPTH, int V, int M32, bool NC = true, bool PF = false>
 __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, const char *y,
                                              char *out, T c, int x0) {
     constexpr MemberTable<D, DEPTH> tab{};
@@ -328,6 +346,12 @@ __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, co
 
 #pragma unroll
     for (int m = 0; m < M; ++m) {
+        if constexpr (PF) {
+            if (m + 1 < M) {
+                if (m + 1 < M32) prefetch_member<T, T, D>(member_t<T, M32>(in, m + 1, a.P), a, x0, idx);
+                else prefetch_member<bf16, T, D>(member_h<T, M32>(in, m + 1, a.P), a, x0, idx);
+            }
+        }
         T k[V], dp[D][V], v[V];
         if (m < M32)
             member_terms<T, T, D, V, NC>(member_t<T, M32>(in, m, a.P), a, x0, idx, Fs, vq, k, dp, v);
@@ -375,13 +399,13 @@ __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, co
     }
 }
 
-template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32>
+template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32, bool PF = false>
 __global__ void __launch_bounds__(NT, MINB) stage_vec_kernel(const StageArgs<T> a) {
     const int x0 = (blockIdx.x * NT + threadIdx.x) * V;
     if (x0 >= a.g.P) return;
     const long long boff = (long long)blockIdx.y * a.state_bytes;
-    stage_points<T, D, DEPTH, V, M32>(a.g, a.in + boff, a.y ? a.y + boff : nullptr, a.out + boff,
-                                      a.c, x0);
+    stage_points<T, D, DEPTH, V, M32, true, PF>(a.g, a.in + boff, a.y ? a.y + boff : nullptr,
+                                                a.out + boff, a.c, x0);
 }
 
 // ------------------------------------------------------------------------------------------

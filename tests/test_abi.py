@@ -54,6 +54,14 @@ def test_create_rejects_invalid_arguments_on_cpu():
     small = inputs.Grid(nq=(6,), np=(64,), qmin=(-6,), qmax=(6,), pmin=(-6,), pmax=(6,))
     with pytest.raises(chfpe.ChfpeError):
         chfpe.Handle(wl.model, small, depth=2, dt=0.005)
+    # the max-index truncation is declared but not built
+    import ctypes
+    m, g = chfpe.make_model(wl.model), chfpe.make_grid(wl.grid)
+    o = chfpe.chfpe_options(depth=wl.depth, precision=32, dt=wl.dt, max_batch=1, truncation=1)
+    h = ctypes.c_void_p()
+    assert chfpe.load().chfpe_create(ctypes.byref(m), ctypes.byref(g), ctypes.byref(o),
+                                     ctypes.byref(h)) == chfpe.EINVAL
+    assert "truncation" in chfpe.last_error() and not h.value
 
 
 def test_surrogate_host_entry_points_on_cpu():
