@@ -35,10 +35,6 @@ struct BulkArgs {
 
 constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;   // 0.2 s per wait
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -73,14 +69,6 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_
         :
         : "r"(dst), "l"(src), "r"(bytes), "r"(bar)
         : "memory");
-}
-
-// 16 bytes global -> shared; src_bytes = 0 writes 16 zero bytes and reads nothing
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                 :
-                 : "r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
 }
 
 // geometry of one block's tile

@@ -234,11 +234,14 @@ __device__ __forceinline__ const bf16 *member_h(const char *base, int m, int P) 
 // one member at V points: its own Liouvillian terms k = sum_s [F_s D_ps g - v_s D_qs g] (the
 // q-derivatives are consumed at once), its p-derivatives dp_s (kept for the hierarchy links) and
 // its values; the p_d derivative comes from a window of (2 NS + 1) vectors
-template <typename S, typename T, int D, int V, bool NC = true>
+// qs != nullptr (QS = threads per block): the q-neighbour vectors come from this thread's
+// shared-memory slots qs[(s * 6 + kk) * QS], kk = 0..5 <-> offsets -3, -2, -1, +1, +2, +3, which
+// hold zeros for neighbours outside the grid (float, V = 4 only)
+template <typename S, typename T, int D, int V, bool NC = true, int QS = 0>
 __device__ __forceinline__ void member_terms(const S *__restrict__ g, const Geo<T> &a, int x0,
                                              const int (&idx)[2 * D], const T (&Fs)[D],
                                              const T (&vq)[D][V], T (&k)[V], T (&dp)[D][V],
-                                             T (&v)[V]) {
+                                             T (&v)[V], const float4 *qs = nullptr) {
     constexpr int NS = (3 + V - 1) / V;          // side vectors of the p_d window
     constexpr int WN = (2 * NS + 1) * V;
     constexpr int L = 2 * D - 1;
@@ -257,7 +260,19 @@ __device__ __forceinline__ void member_terms(const S *__restrict__ g, const Geo<
 #pragma unroll
     for (int s = 0; s < D; ++s) {
         T dq[V];
-        vstencil<S, T, V, NC>(g, x0, idx[s], a.n[s], a.st[s], dq);
+        if constexpr (QS > 0) {
+            static_assert(V == 4, "staged q-neighbours are float4 slots");
+            float4 t[6];
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk) t[kk] = qs[(s * 6 + kk) * QS];
+            const float *p1 = &t[3].x, *m1 = &t[2].x, *p2 = &t[4].x, *m2 = &t[1].x, *p3 = &t[5].x,
+                        *m3 = &t[0].x;
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+                dq[j] = T(45) * (p1[j] - m1[j]) - T(9) * (p2[j] - m2[j]) + (p3[j] - m3[j]);
+        } else {
+            vstencil<S, T, V, NC>(g, x0, idx[s], a.n[s], a.st[s], dq);
+        }
         if (s < D - 1) {
             vstencil<S, T, V, NC>(g, x0, idx[D + s], a.n[D + s], a.st[D + s], dp[s]);
         } else {
@@ -273,6 +288,18 @@ __device__ __forceinline__ void member_terms(const S *__restrict__ g, const Geo<
     }
 #pragma unroll
     for (int j = 0; j < V; ++j) v[j] = w[NS * V + j];
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 16 bytes global -> shared, asynchronous; src_bytes = 0 writes 16 zero bytes and reads nothing
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :
+                 : "r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
 }
 
 // L1 prefetch hint for one member's stencil neighbours along the q axes (in-bounds addresses
@@ -304,11 +331,17 @@ __device__ __forceinline__ void prefetch_member(const S *g, const Geo<T> &a, int
 // window of (2 NS + 1) vectors, NS = ceil(3 / V).
 // ------------------------------------------------------------------------------------------
 
-template <typename T, int D, int DEPTH, int V, int M32, bool NC = true, bool PF = false>
+// QS > 0 (= threads per block; FP32, V = 4, plain storage): each thread stages the q-neighbour
+// vectors of member m + 1 into its own shared-memory slots by cp.async while member m is
+// computed (two slot sets, 6 D float4 each; the thread reads only what it copied itself, so
+// cp.async.wait_group orders everything and no block barrier is needed)
+template <typename T, int D, int DEPTH, int V, int M32, bool NC = true, bool PF = false, int QS = 0>
 __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, const char *y,
                                              char *out, T c, int x0) {
     constexpr MemberTable<D, DEPTH> tab{};
     constexpr int M = MemberTable<D, DEPTH>::M;
+    static_assert(QS == 0 || (V == 4 && M32 == M), "q staging: FP32, 4 points, plain storage");
+    extern __shared__ float4 qslots[];   // [2][6 D][QS]
 
     int idx[2 * D];
     {
@@ -344,8 +377,31 @@ __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, co
 #pragma unroll
         for (int j = 0; j < V; ++j) acc[m][j] = T(0);
 
+    auto q_issue = [&](int mm, int buf) {   // member mm's q-neighbours into slot set buf
+        const T *g = member_t<T, M32>(in, mm, a.P);
+        float4 *slot = qslots + buf * 6 * D * QS + threadIdx.x;
+#pragma unroll
+        for (int s = 0; s < D; ++s)
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk) {
+                const int kq = kk < 3 ? kk - 3 : kk - 2;
+                const bool ok = idx[s] + kq >= 0 && idx[s] + kq < a.n[s];
+                cp_async16(slot + (s * 6 + kk) * QS, ok ? g + x0 + kq * a.st[s] : g, ok ? 16 : 0);
+            }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if constexpr (QS > 0) q_issue(0, 0);
+
 #pragma unroll
     for (int m = 0; m < M; ++m) {
+        if constexpr (QS > 0) {
+            if (m + 1 < M) {
+                q_issue(m + 1, (m + 1) & 1);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");   // member m's slots landed
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+        }
         if constexpr (PF) {
             if (m + 1 < M) {
                 if (m + 1 < M32) prefetch_member<T, T, D>(member_t<T, M32>(in, m + 1, a.P), a, x0, idx);
@@ -353,7 +409,10 @@ __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, co
             }
         }
         T k[V], dp[D][V], v[V];
-        if (m < M32)
+        if constexpr (QS > 0)
+            member_terms<T, T, D, V, NC, QS>(member_t<T, M32>(in, m, a.P), a, x0, idx, Fs, vq, k, dp,
+                                             v, qslots + (m & 1) * 6 * D * QS + threadIdx.x);
+        else if (m < M32)
             member_terms<T, T, D, V, NC>(member_t<T, M32>(in, m, a.P), a, x0, idx, Fs, vq, k, dp, v);
         else
             member_terms<bf16, T, D, V, NC>(member_h<T, M32>(in, m, a.P), a, x0, idx, Fs, vq, k, dp, v);
@@ -399,13 +458,14 @@ __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, co
     }
 }
 
-template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32, bool PF = false>
+template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32, bool PF = false,
+          bool QST = false>
 __global__ void __launch_bounds__(NT, MINB) stage_vec_kernel(const StageArgs<T> a) {
     const int x0 = (blockIdx.x * NT + threadIdx.x) * V;
     if (x0 >= a.g.P) return;
     const long long boff = (long long)blockIdx.y * a.state_bytes;
-    stage_points<T, D, DEPTH, V, M32, true, PF>(a.g, a.in + boff, a.y ? a.y + boff : nullptr,
-                                                a.out + boff, a.c, x0);
+    stage_points<T, D, DEPTH, V, M32, true, PF, QST ? NT : 0>(
+        a.g, a.in + boff, a.y ? a.y + boff : nullptr, a.out + boff, a.c, x0);
 }
 
 // ------------------------------------------------------------------------------------------
