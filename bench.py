@@ -49,6 +49,8 @@ def parse():
                     choices=["two_mode_32", "one_mode_64", "three_mode_20", "sweep"],
                     help="two_mode_32 is the benchmark; the others are secondary measurements")
     ap.add_argument("--instances", type=int, default=64, help="sweep: instances in the batch")
+    ap.add_argument("--error-instances", type=int, default=8,
+                    help="sweep: instances re-run in FP64 for the per-instance error report")
     return ap.parse_args()
 
 
@@ -417,6 +419,24 @@ def run_extra(args, local):
     if args.workload == "three_mode_20":
         line["extrapolated_s_per_128x128_spectrum"] = (inputs.three_mode_20().r2_state_steps() *
                                                         wl.cells / (units * args.steps / T))
+    if args.workload == "sweep" and args.error_instances > 0:
+        # error of the FP32 + bf16-tier propagation against FP64, per instance: the first
+        # instances, from the same stored equilibria, R1 over 200 steps (21 samples)
+        ne = min(args.error_instances, len(wls))
+        sub = wls[:ne]
+        Ws = [h.instance(i).get_equilibrium() for i in range(ne)]
+        R = {}
+        for prec_e, tier in ((32, 3), (64, 0)):
+            with chfpe.Batch([w.model for w in sub], [w.grid for w in sub], depth=4, dt=0.005,
+                             precision=prec_e, stream=stream.cuda_stream, bf16_tier=tier) as be:
+                for i in range(ne):
+                    be.instance(i).set_equilibrium(Ws[i])
+                R[prec_e] = be.response1_all(mu, mu, 21, 10)
+        errs = [float(np.abs(R[32][i] - R[64][i]).max() / np.abs(R[64][i]).max()) for i in range(ne)]
+        line["error_vs_fp64"] = {
+            "instances": ne, "steps": 200, "metric": "max_t |R1_f32+bf16 - R1_f64| / max_t |R1_f64|",
+            "median": float(np.median(errs)), "max": float(np.max(errs)),
+            "per_instance": [float("%.3g" % e) for e in errs]}
     print(json.dumps(line), flush=True)
     h.close()
 

@@ -491,12 +491,21 @@ struct BatchStageArgs {
 
 template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32>
 __global__ void __launch_bounds__(NT, MINB) stage_batch_kernel(const BatchStageArgs<T> b) {
+    // the block's instance geometry, copied once into shared memory: every thread reads its
+    // sizes, strides and coefficients many times
+    __shared__ __align__(16) InstGeo<T> sg;
+    static_assert(sizeof(InstGeo<T>) % 4 == 0 && sizeof(InstGeo<T>) / 4 <= 4 * NT, "geometry copy");
     const int2 item = b.work[blockIdx.x];
-    const InstGeo<T> &ig = b.inst[item.x];
+    {
+        const unsigned *src = reinterpret_cast<const unsigned *>(b.inst + item.x);
+        unsigned *dst = reinterpret_cast<unsigned *>(&sg);
+        for (int w = threadIdx.x; w < (int)(sizeof(InstGeo<T>) / 4); w += NT) dst[w] = __ldg(src + w);
+    }
+    __syncthreads();
     const int x0 = (item.y * NT + threadIdx.x) * V;
-    if (x0 >= ig.g.P) return;
-    const long long off = ig.off;
-    stage_points<T, D, DEPTH, V, M32>(ig.g, b.in + off, b.y ? b.y + off : nullptr, b.out + off,
+    if (x0 >= sg.g.P) return;
+    const long long off = sg.off;
+    stage_points<T, D, DEPTH, V, M32>(sg.g, b.in + off, b.y ? b.y + off : nullptr, b.out + off,
                                       b.c, x0);
 }
 
