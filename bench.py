@@ -32,7 +32,7 @@ ELEM_ACCESSES_PER_CELL_STEP = 11      # Horner-form RK4: 2 + 3 + 3 + 3 element a
 # points per thread, threads per block, minimum resident blocks per SM), as in chfpe.cu
 STAGE_SHAPES = {0: (2, 128, 8), 1: (2, 256, 4), 2: (2, 128, 6), 3: (4, 128, 4), 4: (4, 128, 4), 5: (4, 128, 4),
                 6: (4, 256, 2), 7: (4, 64, 8), 8: (4, 128, 4),
-                9: (4, 128, 4)}
+                9: (4, 128, 4), 10: (4, 128, 3), 11: (4, 128, 2)}
 
 
 def parse():

@@ -282,19 +282,20 @@ chfpe_status chfpe_surrogate_gemm(const void *A, int ta, int lda, const void *B,
  * (modes, depth) = (1, 5), (2, 2), (2, 4), (3, 2), chfpe_create times every shape on zeroed
  * scratch arenas of the handle (up to 4 branch states, else the chain's work arrays; three
  * launches each after one warm-up) and keeps the fastest; every other handle uses shape 0.
- * The environment variable CHFPE_STAGE_VARIANT=k (0..9) forces shape k.  Shapes: 0 two points
+ * The environment variable CHFPE_STAGE_VARIANT=k (0..11) forces shape k.  Shapes: 0 two points
  * per thread, 128 threads; 1 the same with 256 threads; 2 two points with a larger register
  * budget; 3 four points per thread; 4 four points per thread with each member's tile staged in
  * shared memory by bulk asynchronous copies, double-buffered across members (two modes only);
  * 5 as 4 with the shared-memory buffers filled by 16-byte asynchronous copies of every thread;
  * 6 and 7 as 3 with 256 and 64 threads per block; 8 as 3 with L1 prefetch hints for the next
  * member's q-neighbours; 9 as 3 with the next member's q-neighbours copied asynchronously into
- * per-thread shared-memory slots.  Shapes 3-9 need the last p extent to be a multiple of 4 and
- * fall back to shape 0 otherwise.
+ * per-thread shared-memory slots; 10 and 11 as 3 with register budgets for 3 and 2 blocks per
+ * SM.  Shapes 3-11 need the last p extent to be a multiple of 4 and fall back to shape 0
+ * otherwise.
  * All shapes compute the same arithmetic in the same order.  Shape 4's waits are bounded; a wait
  * that gives up makes the next synchronising call return CHFPE_ETIMEOUT.
  */
-#define CHFPE_STAGE_VARIANTS 10
+#define CHFPE_STAGE_VARIANTS 12
 /* The chosen shape and the measured microseconds per stage launch of each shape (-1: not timed);
  * us may be NULL, else it receives CHFPE_STAGE_VARIANTS doubles.  For a batch
  * (chfpe_create_batch) the instances fall into size classes by their last p extent (multiple of

@@ -181,6 +181,8 @@ static int bf16_m32(int d, int depth, int tier) {
 //   8  shape 3 with L1 prefetch hints for the next member's q-neighbours
 //   9  shape 3 with the next member's q-neighbours staged by cp.async in thread-private shared
 //      memory slots (no block barrier)
+//  10  shape 3 with registers for 3 blocks per SM (168)
+//  11  shape 3 with registers for 2 blocks per SM (255)
 constexpr bool tunable(int T_size, int D, int DEPTH) {
     return T_size == 4 && ((D == 1 && DEPTH == 5) || (D == 2 && (DEPTH == 2 || DEPTH == 4)) ||
                            (D == 3 && DEPTH == 2));
@@ -249,6 +251,8 @@ static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int varia
         case 7: launch_vec<T, D, DEPTH, M32, 4, 64, 8>(a, batch, s); return;
         case 8: launch_vec<T, D, DEPTH, M32, 4, 128, 4, true>(a, batch, s); return;
         case 9: launch_vec<T, D, DEPTH, M32, 4, 128, 4, false, true>(a, batch, s); return;
+        case 10: launch_vec<T, D, DEPTH, M32, 4, 128, 3>(a, batch, s); return;
+        case 11: launch_vec<T, D, DEPTH, M32, 4, 128, 2>(a, batch, s); return;
         case 4:
         case 5:
             if constexpr (D == 2) {

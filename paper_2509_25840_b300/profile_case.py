@@ -21,7 +21,7 @@ def main():
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
-    ap.add_argument("--variant", type=int, default=None, choices=range(10))
+    ap.add_argument("--variant", type=int, default=None, choices=range(12))
     a = ap.parse_args()
     if a.variant is not None:
         os.environ["CHFPE_STAGE_VARIANT"] = str(a.variant)
