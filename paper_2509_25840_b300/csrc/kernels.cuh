@@ -3,15 +3,17 @@
 // All kernels work on the symmetrised members g^(n) = W^(n) exp(H/2kT) / lambda_n (Appendix A's
 // exp(-H/2kT) prefactor) stored [batch][member][q_1..q_d][p_1..p_d], p_d fastest.
 //
-//   stage_kernel    out = y + c * (M in)   (or out = M in when y == nullptr), where M is the
+//   stage_vec_kernel, stage_batch_kernel (and persistent.cuh, bulk.cuh)
+//                   out = y + c * (M in)   (or out = M in when y == nullptr), where M is the
 //                   right-hand side of Eq. HEOM in symmetrised form:
 //                     (M g)^(n) = sum_s [dU/dq_s D_ps g^(n) - (p_s/m_s) D_qs g^(n)]
 //                               - sum_s n_s gamma_s g^(n)
 //                               + sum_s sqrt((n_s+1)c_s) V_s' (D_ps - p_s/2m_skT) g^(n+e_s)
 //                               + sum_s sqrt(n_s c_s)     V_s' (D_ps + p_s/2m_skT) g^(n-e_s)
 //                   (Eqs. CL_liouville, Phi, Theta; c_s = zeta_s gamma_s m_s kT).  One thread
-//                   owns one grid point for every member: each member's p-derivatives are formed
-//                   once and pushed to the member itself and to its two neighbours per mode.
+//                   owns V consecutive p_d points of one row for every member: each member's
+//                   p-derivatives are formed once and pushed to the member itself and to its two
+//                   neighbours per mode.
 //   insert_kernel   out^(n) = sum_s dX/dq_s (D_ps - p_s/2m_skT) g^(n)      (Eq. Opticalexc)
 //   observe_*       R = h^2d sum C(q) exp(-H/2kT) g^(0), FP64 accumulation, two passes
 //                   (per-block partials, then a fixed-order sum: deterministic)
