@@ -254,7 +254,8 @@ def run_ours(args, rank, world, local, pg):
     variant, tune_us = h.stage_tuning()
     V, NT, MINB = STAGE_SHAPES[variant]
     kernel = ("stage_bulk_kernel<4,128>" if variant == 4 else "stage_cpasync_kernel<4,128>" if variant == 5 else
-              "stage_vec_kernel<float,2,4,%d,%d,%d,15>" % (V, NT, MINB))
+              "stage_vec_kernel<float,2,4,%d,%d,%d,15,%d,%d>" % (V, NT, MINB, int(variant == 8),
+                                                               int(variant == 9)))
     # DRAM bytes per launch from the committed ncu capture of this kernel: measured bytes per
     # cell-stage times the cells of one branch-phase launch (nt1 states)
     traffic = None
