@@ -143,17 +143,20 @@ chfpe_status chfpe_load_equilibrium(chfpe_handle *h, const char *path);
 
 /* Create a batch of n instances (models[i], grids[i]) sharing one set of options (same number of
  * modes, depth, precision, bf16_tier; max_batch is ignored).  Every RK4 stage of every instance is
- * one launch over a work list of (instance, tile) items.  One step of the batch is nsub substeps
- * of dt / nsub, nsub the smallest power of two keeping every instance inside the RK4 stability
- * bound (A15: a stiff instance lowers the step of the batch instead of failing).  Instance states
- * live in batch-owned arenas; destroy the batch with chfpe_destroy (it destroys the instances). */
+ * one launch over a work list of (instance, tile) items.  Instance i steps dt / nsub_i, nsub_i the
+ * smallest power of two keeping it inside the RK4 stability bound (A15: a stiff instance
+ * substeps instead of failing); one step dt of the batch is nsub = max nsub_i substep slots, and
+ * instance i takes part in every (nsub / nsub_i)-th slot only, so a stiff instance costs the other
+ * instances nothing.  Each instance's stage coefficients are its own, formed as a single handle
+ * with that dt forms them.  Instance states live in batch-owned arenas; destroy the batch with
+ * chfpe_destroy (it destroys the instances). */
 chfpe_status chfpe_create_batch(int n, const chfpe_model *models, const chfpe_grid *grids,
                                 const chfpe_options *opts, chfpe_handle **out);
 /* Borrow instance i of a batch (owned by the batch: do not destroy) for per-instance calls:
  * equilibrate, set/get equilibrium or state, response1, propagate. */
 chfpe_status chfpe_batch_instance(chfpe_handle *batch, int i, chfpe_handle **inst);
-/* chfpe_equilibrate on every instance (max_steps and check_every in batch steps); residuals[i]
- * (may be NULL) receives instance i's last residual. */
+/* chfpe_equilibrate on every instance (max_steps and check_every in steps of dt; instance i runs
+ * nsub_i times as many of its own steps); residuals[i] (may be NULL) receives its last residual. */
 chfpe_status chfpe_batch_equilibrate(chfpe_handle *batch, long max_steps, double tol,
                                      long check_every, double *residuals);
 /* R1 (Eq. 1Dresponse) of every instance from its equilibrium: R[i * nt + k] (host, caller-owned),

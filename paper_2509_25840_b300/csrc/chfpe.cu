@@ -107,9 +107,17 @@ struct chfpe_handle {
     std::vector<long long> inst_off;    // byte offset of each instance in the batch arenas
     int nsub = 1;                       // RK4 substeps per requested step (dt / nsub per step)
     void *d_geo = nullptr;              // InstGeo<T>[n]
-    // work lists by tile shape: [0] 4 points per thread, [1] 2 points, [2] 1 point
+    // work lists by tile shape: [0] 4 points per thread, [1] 2 points, [2] 1 point (the lists of
+    // the current substep level; they alias lv_ptr once the batch is set up)
     int2 *d_work[3] = {nullptr, nullptr, nullptr};
     int nwork[3] = {0, 0, 0};
+    // per-instance substeps: instance i steps dt / nsub_i, taking part in substep slots j of a
+    // nominal step with j % (nsub / nsub_i) == 0; level l holds the instances whose period
+    // nsub / nsub_i divides 2^l (level log2(nsub) = every instance)
+    std::vector<int2 *> lv_ptr;         // [level * 3 + list]
+    std::vector<int> lv_n;
+    std::vector<double> lv_bytes, lv_cells;
+    int nlevels = 0;
     double cells_total = 0.0;
 };
 
@@ -688,9 +696,14 @@ extern "C" void chfpe_destroy(chfpe_handle *h) {
     if (h->borrowed_arenas) h->cy = h->ca = h->cb = h->eq = nullptr;
     void *ptrs[] = {h->U_d, h->F_d, h->F_f, h->wp, h->CWq, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
                     h->cy, h->ca, h->cb, h->by, h->ba, h->bb, h->eq, h->stage64, h->partial, h->dR,
-                    h->counter, h->d_err, h->d_bar, h->d_geo, h->d_work[0], h->d_work[1], h->d_work[2]};
+                    h->counter, h->d_err, h->d_bar, h->d_geo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (h->lv_ptr.empty()) {            // work lists still owned by d_work (set-up failed)
+        for (int2 *p : h->d_work) if (p) cudaFree(p);
+    } else {
+        for (int2 *p : h->lv_ptr) if (p) cudaFree(p);
+    }
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -1516,13 +1529,15 @@ static bool launch_batch_t(const chfpe_handle *b, const BatchStageArgs<T> &a) {
 
 // one RK4 stage over every instance of the batch: out = y + c M in  (arena base pointers)
 template <typename T>
-static chfpe_status batch_stage(chfpe_handle *b, const void *in, const void *y, void *out, double c) {
+static chfpe_status batch_stage(chfpe_handle *b, const void *in, const void *y, void *out, int stage,
+                                double c = 0.0) {
     BatchStageArgs<T> a;
     a.inst = (const InstGeo<T> *)b->d_geo;
     a.work = nullptr;
     a.in = (const char *)in;
     a.y = (const char *)y;
     a.out = (char *)out;
+    a.stage = stage;
     a.c = (T)c;
     bool ok;
 #define CASE(D_, K_) \
@@ -1541,26 +1556,40 @@ static chfpe_status batch_stage(chfpe_handle *b, const void *in, const void *y, 
     return CHFPE_OK;
 }
 
+// point the current work lists at substep level l
+static void use_level(chfpe_handle *b, int l) {
+    for (int k = 0; k < 3; ++k) {
+        b->d_work[k] = b->lv_ptr[l * 3 + k];
+        b->nwork[k] = b->lv_n[l * 3 + k];
+    }
+}
+
+// nslots substep slots (a nominal step of dt is nsub slots; calls start on a nominal step): slot
+// j runs the instances of level (j == 0 ? log2(nsub) : number of trailing zero bits of j), each
+// with its own stage coefficients
 template <typename T>
-static chfpe_status batch_rk4(chfpe_handle *b, long nsteps) {
+static chfpe_status batch_rk4(chfpe_handle *b, long nslots) {
     chfpe_status st;
-    const double dt = b->dt;
-    if (nsteps <= 0) return CHFPE_OK;
+    if (nslots <= 0) return CHFPE_OK;
+    const int top = b->nlevels - 1;
     if (b->time_stages && (st = burst_event(b))) return st;
-    for (long k = 0; k < nsteps; ++k) {
-        if ((st = batch_stage<T>(b, b->cy, b->cy, b->ca, dt / 4.0))) return st;
-        if ((st = batch_stage<T>(b, b->ca, b->cy, b->cb, dt / 3.0))) return st;
-        if ((st = batch_stage<T>(b, b->cb, b->cy, b->ca, dt / 2.0))) return st;
-        if ((st = batch_stage<T>(b, b->ca, b->cy, b->cy, dt))) return st;
+    for (long k = 0; k < nslots; ++k) {
+        const long j = k % b->nsub;
+        const int l = j == 0 ? top : __builtin_ctzl((unsigned long)j);
+        use_level(b, l);
+        if ((st = batch_stage<T>(b, b->cy, b->cy, b->ca, 0))) break;
+        if ((st = batch_stage<T>(b, b->ca, b->cy, b->cb, 1))) break;
+        if ((st = batch_stage<T>(b, b->cb, b->cy, b->ca, 2))) break;
+        if ((st = batch_stage<T>(b, b->ca, b->cy, b->cy, 3))) break;
+        b->cell_updates += b->lv_cells[l];
+        if (b->time_stages) {
+            b->stage_launches += 4 * batch_lists(b);
+            b->stage_bytes += b->lv_bytes[l] * 11.0;
+        }
     }
+    use_level(b, top);
+    if (st) return st;
     if (b->time_stages && (st = burst_event(b))) return st;
-    double bytes = 0.0;
-    for (chfpe_handle *c : b->inst) bytes += (double)c->state_bytes;
-    b->cell_updates += (double)nsteps * b->cells_total;
-    if (b->time_stages) {
-        b->stage_launches += 4 * nsteps * batch_lists(b);
-        b->stage_bytes += (double)nsteps * bytes * 11.0;
-    }
     return CHFPE_OK;
 }
 
@@ -1591,6 +1620,11 @@ static chfpe_status batch_setup_geo(chfpe_handle *b) {
         geo[i].g = geo_of<T>(b->inst[i]);
         geo[i].off = b->inst_off[i];
         const chfpe_handle *c = b->inst[i];
+        // the instance's own step dt_i = dt / nsub_i, coefficients formed as rk4() forms them
+        geo[i].cst[0] = (T)(c->dt / 4.0);
+        geo[i].cst[1] = (T)(c->dt / 3.0);
+        geo[i].cst[2] = (T)(c->dt / 2.0);
+        geo[i].cst[3] = (T)c->dt;
         const int npd = c->n[2 * c->d - 1];
         auto tiles = [&](int per_tile, std::vector<int2> &w) {
             for (int t = 0; t < (c->P + per_tile - 1) / per_tile; ++t) w.push_back(make_int2(i, t));
@@ -1625,9 +1659,9 @@ static chfpe_status batch_setup_geo(chfpe_handle *b) {
                 if ((st = set_work(b, 0, k == 0 ? w4 : std::vector<int2>()))) break;
                 if ((st = set_work(b, 1, k == 1 ? w4as2 : std::vector<int2>()))) break;
                 if ((st = set_work(b, 2, std::vector<int2>()))) break;
-                if ((st = batch_stage<T>(b, b->ca, b->cb, b->cb, 1e-3))) break;   // warm-up
+                if ((st = batch_stage<T>(b, b->ca, b->cb, b->cb, -1, 1e-3))) break;   // warm-up
                 e = cudaEventRecord(e0, b->stream);
-                for (int r = 0; r < 2 && e == cudaSuccess && !st; ++r) st = batch_stage<T>(b, b->ca, b->cb, b->cb, 1e-3);
+                for (int r = 0; r < 2 && e == cudaSuccess && !st; ++r) st = batch_stage<T>(b, b->ca, b->cb, b->cb, -1, 1e-3);
                 if (st) break;
                 if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1645,11 +1679,47 @@ static chfpe_status batch_setup_geo(chfpe_handle *b) {
         b->launches = 0;
     }
     if (four) b->variant = 3;
-    std::vector<int2> l2 = w2;
-    if (!four) l2.insert(l2.end(), w4as2.begin(), w4as2.end());
-    if ((st = set_work(b, 0, four ? w4 : std::vector<int2>()))) return st;
-    if ((st = set_work(b, 1, l2))) return st;
-    if ((st = set_work(b, 2, w1))) return st;
+    for (int k = 0; k < 3; ++k)                           // the tuning lists are not kept
+        if ((st = set_work(b, k, std::vector<int2>()))) return st;
+    // work lists per substep level: level l holds the instances whose period nsub / nsub_i
+    // divides 2^l (the top level, log2(nsub), holds every instance)
+    int top = 0;
+    while ((1 << top) < b->nsub) ++top;
+    b->nlevels = top + 1;
+    b->lv_ptr.assign(3 * b->nlevels, nullptr);
+    b->lv_n.assign(3 * b->nlevels, 0);
+    b->lv_bytes.assign(b->nlevels, 0.0);
+    b->lv_cells.assign(b->nlevels, 0.0);
+    auto period_log = [&](int i) {
+        int p = 0;
+        while ((b->inst[i]->nsub << p) < b->nsub) ++p;
+        return p;
+    };
+    for (int l = 0; l < b->nlevels; ++l) {
+        std::vector<int2> lists[3];
+        auto take = [&](const std::vector<int2> &src, std::vector<int2> &dst) {
+            for (const int2 &w : src)
+                if (period_log(w.x) <= l) dst.push_back(w);
+        };
+        if (four) take(w4, lists[0]);
+        take(w2, lists[1]);
+        if (!four) take(w4as2, lists[1]);
+        take(w1, lists[2]);
+        for (int k = 0; k < 3; ++k) {
+            b->lv_n[l * 3 + k] = (int)lists[k].size();
+            if (lists[k].empty()) continue;
+            b->lv_ptr[l * 3 + k] = dalloc<int2>(lists[k].size(), &st);
+            if (st) return st;
+            CK(cudaMemcpyAsync(b->lv_ptr[l * 3 + k], lists[k].data(), lists[k].size() * sizeof(int2),
+                               cudaMemcpyHostToDevice, b->stream));
+        }
+        for (int i = 0; i < n; ++i)
+            if (period_log(i) <= l) {
+                b->lv_bytes[l] += (double)b->inst[i]->state_bytes;
+                b->lv_cells[l] += (double)b->inst[i]->state;
+            }
+    }
+    use_level(b, top);
     CK(cudaStreamSynchronize(b->stream));
     return CHFPE_OK;
 }
@@ -1665,12 +1735,14 @@ extern "C" chfpe_status chfpe_create_batch(int n, const chfpe_model *models, con
         if (models[i].nmodes != models[0].nmodes)
             return fail(CHFPE_EINVAL, "all instances of a batch must have the same number of modes");
     }
-    // one RK4 step of the batch = nsub substeps of dt / nsub, nsub the smallest power of two that
-    // keeps every instance inside the stability bound
+    // instance i steps dt / nsub_i, nsub_i the smallest power of two that keeps it inside the
+    // stability bound; a nominal step of the batch is nsub = max nsub_i substep slots
+    std::vector<int> nsub_i(n, 1);
     int nsub = 1;
     for (int i = 0; i < n; ++i) {
         const double rho = bound_for(&models[i], &grids[i], opts->depth);
-        while (opts->dt / nsub * rho > 2.6 && nsub < (1 << 12)) nsub *= 2;
+        while (opts->dt / nsub_i[i] * rho > 2.6 && nsub_i[i] < (1 << 12)) nsub_i[i] *= 2;
+        nsub = std::max(nsub, nsub_i[i]);
     }
     chfpe_handle *b = new chfpe_handle();
     b->model = models[0];
@@ -1698,8 +1770,10 @@ extern "C" chfpe_status chfpe_create_batch(int n, const chfpe_model *models, con
     long long total = 0;
     for (int i = 0; i < n && !st; ++i) {
         chfpe_handle *c = nullptr;
+        io.dt = opts->dt / nsub_i[i];
         st = create_impl(&models[i], &grids[i], &io, true, &c);
         if (st) { st = fail(st, "instance " + std::to_string(i) + ": " + g_err); break; }
+        c->nsub = nsub_i[i];
         b->inst.push_back(c);
         b->inst_off.push_back(total);
         total += (c->state_bytes + 255) / 256 * 256;
@@ -1737,8 +1811,8 @@ extern "C" chfpe_status chfpe_batch_equilibrate(chfpe_handle *b, long max_steps,
     if (!b || b->inst.empty()) return fail(CHFPE_EINVAL, "not a batch handle");
     for (size_t i = 0; i < b->inst.size(); ++i) {
         double r = 0.0;
-        chfpe_status st = chfpe_equilibrate(b->inst[i], max_steps * b->nsub, tol,
-                                            check_every * b->nsub, nullptr, &r);
+        chfpe_status st = chfpe_equilibrate(b->inst[i], max_steps * b->inst[i]->nsub, tol,
+                                            check_every * b->inst[i]->nsub, nullptr, &r);
         if (st) return fail(st, "instance " + std::to_string(i) + ": " + g_err);
         if (residuals) residuals[i] = r;
     }
@@ -1785,6 +1859,7 @@ extern "C" chfpe_status chfpe_batch_response1(chfpe_handle *b, const chfpe_optic
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         // instances share the batch stream, so their observation kernels are captured too
+        const double cells0 = b->cell_updates;
         CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         st = advance();
         if (!st) st = observe_all(0, b->counter);
@@ -1798,7 +1873,7 @@ extern "C" chfpe_status chfpe_batch_response1(chfpe_handle *b, const chfpe_optic
         for (int k = 1; k < nt && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, b->stream);
         cudaGraphExecDestroy(exec);
         if (e != cudaSuccess) return fail(CHFPE_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
-        b->cell_updates += (double)(nt - 2) * steps * b->cells_total;
+        b->cell_updates += (double)(nt - 2) * (b->cell_updates - cells0);   // one interval captured
     }
     return finish_response(b, R, (size_t)n * nt);
 }

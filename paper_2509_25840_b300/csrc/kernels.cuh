@@ -479,6 +479,7 @@ template <typename T>
 struct InstGeo {
     Geo<T> g;
     long long off;        // byte offset of the instance's state inside each batch arena
+    T cst[4];             // the instance's RK4 stage coefficients dt_i/4, dt_i/3, dt_i/2, dt_i
 };
 
 template <typename T>
@@ -488,6 +489,7 @@ struct BatchStageArgs {
     const char *in;
     const char *y;
     char *out;
+    int stage;            // 0..3: coefficient cst[stage] of each instance; -1: c for all
     T c;
 };
 
@@ -508,7 +510,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_batch_kernel(const BatchStageA
     if (x0 >= sg.g.P) return;
     const long long off = sg.off;
     stage_points<T, D, DEPTH, V, M32>(sg.g, b.in + off, b.y ? b.y + off : nullptr, b.out + off,
-                                      b.c, x0);
+                                      b.stage >= 0 ? sg.cst[b.stage] : b.c, x0);
 }
 
 // ------------------------------------------------------------------------------------------
