@@ -142,7 +142,8 @@ chfpe_status chfpe_load_equilibrium(chfpe_handle *h, const char *path);
 /* ---- batches: many instances (models and grids) advanced together (BASELINE sweep config) -- */
 
 /* Create a batch of n instances (models[i], grids[i]) sharing one set of options (same number of
- * modes, depth, precision, bf16_tier; max_batch is ignored).  Every RK4 stage of every instance is
+ * modes, depth, precision, bf16_tier; max_batch = the branch slots per instance that
+ * chfpe_batch_response2 advances together, 0 taken as 1).  Every RK4 stage of every instance is
  * one launch over a work list of (instance, tile) items.  Instance i steps dt / nsub_i, nsub_i the
  * smallest power of two keeping it inside the RK4 stability bound (A15: a stiff instance
  * substeps instead of failing); one step dt of the batch is nsub = max nsub_i substep slots, and
@@ -153,8 +154,14 @@ chfpe_status chfpe_load_equilibrium(chfpe_handle *h, const char *path);
 chfpe_status chfpe_create_batch(int n, const chfpe_model *models, const chfpe_grid *grids,
                                 const chfpe_options *opts, chfpe_handle **out);
 /* Borrow instance i of a batch (owned by the batch: do not destroy) for per-instance calls:
- * equilibrate, set/get equilibrium or state, response1, propagate. */
+ * equilibrate, set/get equilibrium or state, response1, propagate.  A borrowed instance steps
+ * its own dt_i = dt / nsub_i (chfpe_time_step): the nsteps, max_steps, check_every and stride
+ * arguments of those calls count steps of dt_i, so two instances given the same count advance
+ * different physical times unless their nsub_i agree. */
 chfpe_status chfpe_batch_instance(chfpe_handle *batch, int i, chfpe_handle **inst);
+/* The RK4 step of a handle: opts->dt for a single handle, dt / nsub_i for instance i of a batch,
+ * dt / max_i nsub_i for the batch itself (its substep slot). */
+chfpe_status chfpe_time_step(const chfpe_handle *h, double *dt);
 /* chfpe_equilibrate on every instance (max_steps and check_every in steps of dt; instance i runs
  * nsub_i times as many of its own steps); residuals[i] (may be NULL) receives its last residual. */
 chfpe_status chfpe_batch_equilibrate(chfpe_handle *batch, long max_steps, double tol,
@@ -163,6 +170,16 @@ chfpe_status chfpe_batch_equilibrate(chfpe_handle *batch, long max_steps, double
  * t = k stride dt, all instances advanced by the same fused launches. */
 chfpe_status chfpe_batch_response1(chfpe_handle *batch, const chfpe_optical *A,
                                    const chfpe_optical *C, int nt, int stride, double *R);
+/* R2 (Eq. 2Dresponse) of every instance from its equilibrium:
+ * R[(i * nt1 + a) * nt2 + b] = integral C G(b stride dt) B^x G(a stride dt) A^x W_eq,i (host,
+ * caller-owned, n * nt1 * nt2 doubles; t in steps of the nominal dt, each instance substepping
+ * as in the batch's RK4).  The t1 chains of all instances advance in the batch's fused launches;
+ * the branches run in chunks of S = min(nt1, max(1, max_batch)) t1 rows, the S branch slots of
+ * every instance advancing together in one launch per RK4 stage.  The first call allocates the
+ * branch arenas (3 x S x the batch's state bytes) and keeps them for later calls. */
+chfpe_status chfpe_batch_response2(chfpe_handle *batch, const chfpe_optical *A,
+                                   const chfpe_optical *B, const chfpe_optical *C, int nt1,
+                                   int nt2, int stride, double *R);
 
 /* Sizes of the handle: members M and points per member P (states are M*P values). */
 chfpe_status chfpe_sizes(const chfpe_handle *h, int *members, long *points);
@@ -181,6 +198,18 @@ chfpe_status chfpe_insert_device(chfpe_handle *h, const chfpe_optical *X, const 
  * of `batch` doubles. */
 chfpe_status chfpe_observe_device(chfpe_handle *h, const chfpe_optical *C, const void *in,
                                   int batch, double *R_dev);
+/* The sampling loop of the response functions (Eq. 1Dresponse; the t2 branch phase of
+ * Eq. 2Dresponse) on caller-owned states: for k = 0..nsamples-1,
+ * R_dev[b*ld + k] = integral C exp(-H/2kT) g^(0) of state b, then -- except after the last
+ * sample -- every state advances `stride` RK4 steps in place.  `states`: `batch` contiguous
+ * device states of the handle's precision and layout (16-byte aligned for the vectorised
+ * kernels; otherwise the scalar kernel runs), 1 <= batch <= max_batch (the handle's branch
+ * arenas are the RK4 work arrays).  R_dev: caller-owned device doubles, ld >= nsamples.  Runs the
+ * same dispatch as chfpe_response1/2 (persistent launch, CUDA-graph intervals or one launch per
+ * stage, by size).  Synchronous.  CHFPE_EINVAL on bad sizes, CHFPE_ETIMEOUT if a bounded device
+ * wait gave up (the states are then undefined), CHFPE_ECUDA. */
+chfpe_status chfpe_sample_device(chfpe_handle *h, const chfpe_optical *C, void *states, int batch,
+                                 int nsamples, int stride, double *R_dev, long ld);
 
 /* ---- reduction without device allocations (no counterpart in the paper) ---------------------- */
 
@@ -285,7 +314,7 @@ chfpe_status chfpe_surrogate_gemm(const void *A, int ta, int lda, const void *B,
  * (modes, depth) = (1, 5), (2, 2), (2, 4), (3, 2), chfpe_create times every shape on zeroed
  * scratch arenas of the handle (up to 4 branch states, else the chain's work arrays; three
  * launches each after one warm-up) and keeps the fastest; every other handle uses shape 0.
- * The environment variable CHFPE_STAGE_VARIANT=k (0..11) forces shape k.  Shapes: 0 two points
+ * The environment variable CHFPE_STAGE_VARIANT=k (0..17) forces shape k.  Shapes: 0 two points
  * per thread, 128 threads; 1 the same with 256 threads; 2 two points with a larger register
  * budget; 3 four points per thread; 4 four points per thread with each member's tile staged in
  * shared memory by bulk asynchronous copies, double-buffered across members (two modes only);
@@ -293,12 +322,17 @@ chfpe_status chfpe_surrogate_gemm(const void *A, int ta, int lda, const void *B,
  * 6 and 7 as 3 with 256 and 64 threads per block; 8 as 3 with L1 prefetch hints for the next
  * member's q-neighbours; 9 as 3 with the next member's q-neighbours copied asynchronously into
  * per-thread shared-memory slots; 10 and 11 as 3 with register budgets for 3 and 2 blocks per
- * SM.  Shapes 3-11 need the last p extent to be a multiple of 4 and fall back to shape 0
- * otherwise.
+ * SM; 12-14 as 3 with a tiled block-to-row mapping (each block covers a small box of grid rows
+ * along (q_{d-1}, q_d, p_{d-1}): 2 x 2 x 4, 1 x 4 x 4, 4 x 4 x 1 rows) so that stencil
+ * neighbours along those axes are mostly loaded by the same block; 15 as 12 with 256 threads
+ * (2 x 4 x 4 box); 16 as 3 and 17 as 12 with each member's result stored as soon as its last
+ * contribution is in.  Shapes 3-17 need the last p extent to be a multiple of 4, and the tiled
+ * shapes (12-15, 17) need a quarter of it to divide the block's thread count; a shape that does
+ * not apply runs shape 0 (and is not timed).
  * All shapes compute the same arithmetic in the same order.  Shape 4's waits are bounded; a wait
  * that gives up makes the next synchronising call return CHFPE_ETIMEOUT.
  */
-#define CHFPE_STAGE_VARIANTS 12
+#define CHFPE_STAGE_VARIANTS 18
 /* The chosen shape and the measured microseconds per stage launch of each shape (-1: not timed);
  * us may be NULL, else it receives CHFPE_STAGE_VARIANTS doubles.  For a batch
  * (chfpe_create_batch) the instances fall into size classes by their last p extent (multiple of

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libchfpe.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
-STAGE_VARIANTS = 12
+STAGE_VARIANTS = 18
 _NAMES = {0: "CHFPE_OK", 1: "CHFPE_EINVAL", 2: "CHFPE_ENOMEM", 3: "CHFPE_ECUDA",
           4: "CHFPE_EUNSTABLE", 5: "CHFPE_ETIMEOUT", 6: "CHFPE_ESTATE"}
 
@@ -101,15 +101,21 @@ def load(path: str = LIB_PATH):
         "chfpe_rk4_device": ([_H, _VP, ctypes.c_int, ctypes.c_long], S),
         "chfpe_insert_device": ([_H, ctypes.POINTER(chfpe_optical), _VP, _VP, ctypes.c_int], S),
         "chfpe_observe_device": ([_H, ctypes.POINTER(chfpe_optical), _VP, ctypes.c_int, _VP], S),
+        "chfpe_sample_device": ([_H, ctypes.POINTER(chfpe_optical), _VP, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, _VP, ctypes.c_long], S),
         "chfpe_observe_noalloc": ([ctypes.POINTER(chfpe_model), ctypes.POINTER(chfpe_grid),
                                    ctypes.c_int, ctypes.c_int, ctypes.POINTER(chfpe_optical),
                                    _VP, ctypes.c_int, _VP, _VP], S),
         "chfpe_create_batch": ([ctypes.c_int, ctypes.POINTER(chfpe_model), ctypes.POINTER(chfpe_grid),
                                 ctypes.POINTER(chfpe_options), ctypes.POINTER(_H)], S),
         "chfpe_batch_instance": ([_H, ctypes.c_int, ctypes.POINTER(_H)], S),
+        "chfpe_time_step": ([_H, _DP], S),
         "chfpe_batch_equilibrate": ([_H, ctypes.c_long, ctypes.c_double, ctypes.c_long, _DP], S),
         "chfpe_batch_response1": ([_H, ctypes.POINTER(chfpe_optical), ctypes.POINTER(chfpe_optical),
                                    ctypes.c_int, ctypes.c_int, _DP], S),
+        "chfpe_batch_response2": ([_H, ctypes.POINTER(chfpe_optical), ctypes.POINTER(chfpe_optical),
+                                   ctypes.POINTER(chfpe_optical), ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, _DP], S),
         "chfpe_stats_reset": ([_H, ctypes.c_int], S),
         "chfpe_stats_get": ([_H, ctypes.POINTER(chfpe_stats)], S),
         "chfpe_last_error": ([], ctypes.c_char_p),
@@ -287,6 +293,12 @@ class Handle:
         _check(load().chfpe_get_state(self._h, _dptr(out)))
         return out
 
+    def time_step(self) -> float:
+        """chfpe_time_step: this handle's RK4 step (dt / nsub_i for a batch instance)."""
+        v = ctypes.c_double()
+        _check(load().chfpe_time_step(self._h, ctypes.byref(v)))
+        return v.value
+
     def propagate(self, nsteps: int):
         _check(load().chfpe_propagate(self._h, int(nsteps)))
 
@@ -334,6 +346,15 @@ class Handle:
         c = make_optical(C)
         _check(load().chfpe_observe_device(self._h, ctypes.byref(c), in_ptr, int(batch), R_ptr))
 
+    def sample_device(self, C, states_ptr: int, batch: int, nsamples: int, stride: int,
+                      R_ptr: int, ld: int | None = None):
+        """chfpe_sample_device: observe C every `stride` RK4 steps of `batch` device states
+        (nsamples samples, the states advance in place) into device doubles R[b * ld + k]."""
+        c = make_optical(C)
+        _check(load().chfpe_sample_device(self._h, ctypes.byref(c), states_ptr, int(batch),
+                                          int(nsamples), int(stride), R_ptr,
+                                          int(nsamples if ld is None else ld)))
+
     # -- counters ---------------------------------------------------------------------------------
     def stats_reset(self, time_stages: bool = False):
         _check(load().chfpe_stats_reset(self._h, int(bool(time_stages))))
@@ -349,13 +370,13 @@ class Batch(Handle):
     stage; instance(i) gives the borrowed per-instance handle."""
 
     def __init__(self, models, grids, depth: int, dt: float, precision: int = 32,
-                 stream: int | None = None, bf16_tier: int = 0):
+                 stream: int | None = None, bf16_tier: int = 0, max_batch: int = 0):
         lib = load()
         n = len(models)
         self._ms = (chfpe_model * n)(*[make_model(m) for m in models])
         self._gs = (chfpe_grid * n)(*[make_grid(g) for g in grids])
         self._o = chfpe_options(depth=int(depth), precision=int(precision), dt=float(dt),
-                                max_batch=0, stream=stream, bf16_tier=int(bf16_tier))
+                                max_batch=int(max_batch), stream=stream, bf16_tier=int(bf16_tier))
         h = _H()
         _check(lib.chfpe_create_batch(n, self._ms, self._gs, ctypes.byref(self._o), ctypes.byref(h)))
         self._h = h
@@ -383,6 +404,16 @@ class Batch(Handle):
         a, c = make_optical(A), make_optical(C)
         _check(load().chfpe_batch_response1(self._h, ctypes.byref(a), ctypes.byref(c), int(nt),
                                             int(stride), _dptr(R)))
+        return R
+
+    def response2_all(self, A, B, C, nt1: int, nt2: int, stride: int) -> np.ndarray:
+        """chfpe_batch_response2: R[i, a, b] of every instance (branches batched across the
+        instances, max_batch t1 rows per chunk)."""
+        R = np.empty((self.n, nt1, nt2))
+        a, b, c = make_optical(A), make_optical(B), make_optical(C)
+        _check(load().chfpe_batch_response2(self._h, ctypes.byref(a), ctypes.byref(b),
+                                            ctypes.byref(c), int(nt1), int(nt2), int(stride),
+                                            _dptr(R)))
         return R
 
     def close(self):

@@ -3,7 +3,7 @@
 // kernels.cuh; host code here validates, sizes, launches and copies.
 #include "../../include/chfpe.h"
 #include "kernels.cuh"
-#include "bulk.cuh"
+#include "stage_launch.cuh"
 #include "persistent.cuh"
 
 #include <cuda_runtime.h>
@@ -102,6 +102,13 @@ struct chfpe_handle {
 
     // instance of a batch: its state arenas are slices of the batch's arenas
     bool borrowed_arenas = false;
+    // branch batch of a batch's R2 (chfpe_batch_response2): its instance list repeats the
+    // batch's instances (not owned), one entry per branch slot
+    bool inst_borrowed = false;
+    chfpe_handle *branches = nullptr;   // owned by the batch; built on first use
+    int branch_cap = 0;                 // branch slots per instance
+    std::vector<long long> branch_base; // byte offset of instance i's first slot
+    std::vector<long long> branch_pitch;// bytes between consecutive slots of instance i
     // batch (chfpe_create_batch): instances share the stream; one launch per RK4 stage
     std::vector<chfpe_handle *> inst;
     std::vector<long long> inst_off;    // byte offset of each instance in the batch arenas
@@ -160,145 +167,17 @@ static StageArgs<T> stage_args(const chfpe_handle *h) {
     return a;
 }
 
-// Vectorised stage kernel shape: two consecutive p_d points per thread (float2 / double2), 128
-// threads per block, registers capped so that 8 blocks (32 warps) fit on an SM for hierarchies
-// of up to 15 members (4 blocks beyond).  Measured on the 32^4 x 15 workload: occupancy beats
-// per-thread reuse here (float4 at 8 warps/SM: 1.6 TB/s; float2 at 32 warps/SM: 2.0 TB/s).
-constexpr int kVec = 2;
-
 // BF16 storage of deep tiers is compiled for these (d, depth, first bf16 member) combinations
 // (FP32 path only): two modes, depth 4, tiers 3-4 (9 of 15 members); three modes, depth 2,
 // tier 2 (6 of 10 members).
+static_assert(kStageVariants == CHFPE_STAGE_VARIANTS, "launch shapes and the ABI agree");
+
 static int bf16_m32(int d, int depth, int tier) {
     if (d == 2 && depth == 4 && tier == 3) return 6;
     if (d == 3 && depth == 2 && tier == 2) return 4;
     return -1;
 }
 
-// Launch shapes the autotuner chooses from (FP32, plain storage, the workload hierarchies
-// (d, depth) = (1, 5), (2, 2), (2, 4), (3, 2); every other configuration uses shape 0):
-//   0  2 points per thread, 128 threads, registers for 8 blocks per SM (4 beyond 15 members)
-//   1  2 points per thread, 256 threads, same registers per thread (more p_1 rows per block)
-//   2  2 points per thread, 128 threads, registers for 6 blocks per SM (fewer spills)
-//   3  4 points per thread, 128 threads, registers for 4 blocks per SM (needs n_pd % 4 == 0)
-//   4  shape 3 with every member's tile staged in shared memory by bulk async copies, double
-//      buffered across members (two modes only; bulk.cuh)
-//   5  shape 4 with the buffers filled by every thread's 16-byte cp.async copies
-//   6  shape 3 with 256 threads (2 blocks per SM)
-//   7  shape 3 with 64 threads (8 blocks per SM)
-//   8  shape 3 with L1 prefetch hints for the next member's q-neighbours
-//   9  shape 3 with the next member's q-neighbours staged by cp.async in thread-private shared
-//      memory slots (no block barrier)
-//  10  shape 3 with registers for 3 blocks per SM (168)
-//  11  shape 3 with registers for 2 blocks per SM (255)
-constexpr bool tunable(int T_size, int D, int DEPTH) {
-    return T_size == 4 && ((D == 1 && DEPTH == 5) || (D == 2 && (DEPTH == 2 || DEPTH == 4)) ||
-                           (D == 3 && DEPTH == 2));
-}
-
-template <typename T, int D, int DEPTH, int M32, int V, int NT, int MINB, bool PF = false,
-          bool QST = false>
-static void launch_vec(const StageArgs<T> &a, int batch, cudaStream_t s) {
-    const int nthr = a.g.P / V;
-    auto kern = stage_vec_kernel<T, D, DEPTH, V, NT, MINB, M32, PF, QST>;
-    size_t smem = 0;
-    if constexpr (QST) {   // two slot sets of 6 D float4 per thread
-        smem = (size_t)2 * 6 * D * NT * sizeof(float4);
-        static bool configured = false;
-        if (!configured) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            configured = true;
-        }
-    }
-    kern<<<dim3((nthr + NT - 1) / NT, batch), NT, smem, s>>>(a);
-}
-
-constexpr int kBulkNT = 128, kBulkTP = kBulkNT * 4;
-
-static BulkArgs bulk_args(const Geo<float> &g, int *err) {
-    BulkArgs b;
-    b.tiles_per_plane = (g.Pp + kBulkTP - 1) / kBulkTP;
-    b.H = 3 * g.n[3];
-    b.buf_floats = kBulkTP + 2 * b.H + 12 * kBulkTP;
-    b.err = err;
-    return b;
-}
-
-static bool bulk_ok(const Geo<float> &g) { return g.n[3] % 4 == 0; }
-
-// shapes 4 (bulk async copies) and 5 (16-byte cp.async) of two-mode hierarchies
-template <int DEPTH, bool CPASYNC>
-static void launch_bulk(const StageArgs<float> &a, int batch, int *err, cudaStream_t s) {
-    const BulkArgs b = bulk_args(a.g, err);
-    const size_t smem = (size_t)2 * b.buf_floats * sizeof(float);
-    auto kern = CPASYNC ? stage_cpasync_kernel<DEPTH, kBulkNT> : stage_bulk_kernel<DEPTH, kBulkNT>;
-    static size_t configured = 0;   // largest dynamic shared memory opted into so far
-    if (smem > configured) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = smem;
-    }
-    kern<<<dim3(a.g.NQ * b.tiles_per_plane, batch), kBulkNT, smem, s>>>(a, b);
-}
-
-template <typename T, int D, int DEPTH, int M32>
-static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int variant, int *err,
-                           cudaStream_t s) {
-    constexpr int M = member_count(D, DEPTH);
-    constexpr int MINB = (sizeof(T) == 4 && M <= 15) ? 8 : 4;
-    if (!vec) {
-        stage_vec_kernel<T, D, DEPTH, 1, 128, 4, M32>
-            <<<dim3((a.g.P + 127) / 128, batch), 128, 0, s>>>(a);
-        return;
-    }
-    if constexpr (tunable(sizeof(T), D, DEPTH) && M32 == M) {
-        switch (variant) {
-        case 1: launch_vec<T, D, DEPTH, M32, 2, 256, MINB / 2>(a, batch, s); return;
-        case 2: launch_vec<T, D, DEPTH, M32, 2, 128, 6>(a, batch, s); return;
-        case 3: launch_vec<T, D, DEPTH, M32, 4, 128, 4>(a, batch, s); return;
-        case 6: launch_vec<T, D, DEPTH, M32, 4, 256, 2>(a, batch, s); return;
-        case 7: launch_vec<T, D, DEPTH, M32, 4, 64, 8>(a, batch, s); return;
-        case 8: launch_vec<T, D, DEPTH, M32, 4, 128, 4, true>(a, batch, s); return;
-        case 9: launch_vec<T, D, DEPTH, M32, 4, 128, 4, false, true>(a, batch, s); return;
-        case 10: launch_vec<T, D, DEPTH, M32, 4, 128, 3>(a, batch, s); return;
-        case 11: launch_vec<T, D, DEPTH, M32, 4, 128, 2>(a, batch, s); return;
-        case 4:
-        case 5:
-            if constexpr (D == 2) {
-                if (bulk_ok(a.g)) {
-                    if (variant == 4) launch_bulk<DEPTH, false>(a, batch, err, s);
-                    else launch_bulk<DEPTH, true>(a, batch, err, s);
-                    return;
-                }
-            }
-            break;
-        default: break;
-        }
-    }
-    launch_vec<T, D, DEPTH, M32, kVec, 128, MINB>(a, batch, s);
-}
-
-template <typename T, int D, int DEPTH>
-static bool launch_stage_t(const StageArgs<T> &a, int batch, bool vec, int M32, int variant,
-                           int *err, cudaStream_t s) {
-    constexpr int M = member_count(D, DEPTH);
-    if (M32 == M) {
-        launch_stage_m<T, D, DEPTH, M>(a, batch, vec, variant, err, s);
-        return true;
-    }
-    if constexpr (sizeof(T) == 4 && D == 2 && DEPTH == 4) {
-        if (M32 == 6) {
-            launch_stage_m<T, D, DEPTH, 6>(a, batch, vec, 0, err, s);
-            return true;
-        }
-    }
-    if constexpr (sizeof(T) == 4 && D == 3 && DEPTH == 2) {
-        if (M32 == 4) {
-            launch_stage_m<T, D, DEPTH, 4>(a, batch, vec, 0, err, s);
-            return true;
-        }
-    }
-    return false;
-}
 
 static bool aligned16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
 
@@ -307,19 +186,15 @@ static bool launch_stage(const chfpe_handle *h, const StageArgs<T> &a, int batch
     cudaStream_t s = h->stream;
     const bool vec = (h->n[2 * h->d - 1] % kVec == 0) && aligned16(a.in) && aligned16(a.y) &&
                      aligned16(a.out) && !h->force_scalar;
-    // shapes 3-7 read 4 consecutive p_d points: only where rows hold whole groups of 4
+    // shapes 3-17 read 4 consecutive p_d points: only where rows hold whole groups of 4
     const int variant = (h->variant >= 3 && h->n[2 * h->d - 1] % 4 != 0) ? 0 : h->variant;
-#define CASE(D_, K_) \
-    case (D_ * 16 + K_): return launch_stage_t<T, D_, K_>(a, batch, vec, m32, variant, h->d_err, s);
     const int m32 = sizeof(T) == 8 ? h->M : h->M32;
-    switch (h->d * 16 + h->depth) {
-        CASE(1, 0) CASE(1, 1) CASE(1, 2) CASE(1, 3) CASE(1, 4) CASE(1, 5) CASE(1, 6) CASE(1, 7)
-        CASE(1, 8)
-        CASE(2, 0) CASE(2, 1) CASE(2, 2) CASE(2, 3) CASE(2, 4) CASE(2, 5)
-        CASE(3, 0) CASE(3, 1) CASE(3, 2) CASE(3, 3)
-        default: return false;
+    switch (h->d) {
+    case 1: return launch_stage_dim<T, 1>(h->depth, a, batch, vec, m32, variant, h->d_err, s);
+    case 2: return launch_stage_dim<T, 2>(h->depth, a, batch, vec, m32, variant, h->d_err, s);
+    case 3: return launch_stage_dim<T, 3>(h->depth, a, batch, vec, m32, variant, h->d_err, s);
+    default: return false;
     }
-#undef CASE
 }
 
 // one stage over `batch` states: out = y + c * M in   (y == nullptr: out = c * M in)
@@ -529,13 +404,14 @@ static int observe_blocks(const chfpe_handle *h) {
 }
 
 static chfpe_status observe(chfpe_handle *h, const void *states, int batch, double *out,
-                            long long out_stride, const int *counter = nullptr) {
+                            long long out_stride, const int *counter = nullptr,
+                            long long state_stride = 0) {
     const int nblk = observe_blocks(h);
     if ((long long)nblk * batch > h->partial_cap) return fail(CHFPE_EINVAL, "batch too large for reduction scratch");
     ObserveArgs a;
     memset(&a, 0, sizeof(a));
     a.in = states;
-    a.state_bytes = h->state_bytes;
+    a.state_bytes = state_stride > 0 ? state_stride : h->state_bytes;
     a.P = h->P;
     a.Pp = h->Pp;
     a.d = h->d;
@@ -692,7 +568,9 @@ static T *dalloc(size_t n, chfpe_status *st) {
 extern "C" void chfpe_destroy(chfpe_handle *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    for (chfpe_handle *c : h->inst) chfpe_destroy(c);
+    if (!h->inst_borrowed)
+        for (chfpe_handle *c : h->inst) chfpe_destroy(c);
+    chfpe_destroy(h->branches);
     if (h->borrowed_arenas) h->cy = h->ca = h->cb = h->eq = nullptr;
     void *ptrs[] = {h->U_d, h->F_d, h->F_f, h->wp, h->CWq, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
                     h->cy, h->ca, h->cb, h->by, h->ba, h->bb, h->eq, h->stage64, h->partial, h->dR,
@@ -876,6 +754,8 @@ static chfpe_status autotune(chfpe_handle *h) {
         for (int v = 0; v < CHFPE_STAGE_VARIANTS && e == cudaSuccess; ++v) {
             if (v >= 3 && npd % 4 != 0) continue;
             if ((v == 4 || v == 5) && h->d != 2) continue;
+            RowTile rt;
+            if (tiled_variant(v) && !row_tile(v, h->d, h->n, &rt)) continue;
             if (round > 0 && h->tune_us[v] < 0) continue;   // disqualified in an earlier round
             h->variant = v;
             launch_stage<float>(h, a, batch);   // warm-up
@@ -1369,6 +1249,23 @@ extern "C" chfpe_status chfpe_observe_device(chfpe_handle *h, const chfpe_optica
     return CHFPE_OK;
 }
 
+// The sampling loop of Eqs. 1Dresponse / 2Dresponse on caller-owned states: the same dispatch
+// (persistent launch, graph-replayed intervals or launch per stage) as the response drivers.
+extern "C" chfpe_status chfpe_sample_device(chfpe_handle *h, const chfpe_optical *C, void *states,
+                                            int batch, int nsamples, int stride, double *R_dev,
+                                            long ld) {
+    if (!h || !C || !states || !R_dev) return fail(CHFPE_EINVAL, "null argument");
+    if (batch < 1 || nsamples < 1 || stride < 0 || ld < nsamples)
+        return fail(CHFPE_EINVAL, "batch >= 1, nsamples >= 1, stride >= 0, ld >= nsamples");
+    if (batch > h->opts.max_batch) return fail(CHFPE_EINVAL, "batch > max_batch");
+    chfpe_status st;
+    if ((st = set_observable(h, C))) return st;
+    if ((st = sampled_propagation(h, states, h->ba, h->bb, batch, nsamples, stride, R_dev, ld)))
+        return st;
+    CK(cudaStreamSynchronize(h->stream));
+    return check_device_error(h);
+}
+
 // ------------------------------------------------------------------------------------------
 // save / load the equilibrium
 // ------------------------------------------------------------------------------------------
@@ -1799,6 +1696,12 @@ extern "C" chfpe_status chfpe_create_batch(int n, const chfpe_model *models, con
     return CHFPE_OK;
 }
 
+extern "C" chfpe_status chfpe_time_step(const chfpe_handle *h, double *dt) {
+    if (!h || !dt) return fail(CHFPE_EINVAL, "null argument");
+    *dt = h->dt;
+    return CHFPE_OK;
+}
+
 extern "C" chfpe_status chfpe_batch_instance(chfpe_handle *b, int i, chfpe_handle **inst) {
     if (!b || !inst) return fail(CHFPE_EINVAL, "null argument");
     if (i < 0 || i >= (int)b->inst.size()) return fail(CHFPE_EINVAL, "instance index out of range");
@@ -1876,4 +1779,128 @@ extern "C" chfpe_status chfpe_batch_response1(chfpe_handle *b, const chfpe_optic
         b->cell_updates += (double)(nt - 2) * (b->cell_updates - cells0);   // one interval captured
     }
     return finish_response(b, R, (size_t)n * nt);
+}
+
+// ------------------------------------------------------------------------------------------
+// R2 of every instance of a batch (Eq. 2Dresponse): the t1 chains of all instances advance
+// together (one launch per RK4 stage over the batch's work lists), and so do the branches: up to
+// `cap` branch slots per instance form a second batch ("branch batch") whose work lists cover
+// every (instance, slot) pair, so one launch per RK4 stage advances the branches of every
+// instance.  Slot c of instance i lives at branch_base[i] + c * branch_pitch[i] in the branch
+// batch's arenas (pitch = state bytes rounded up to 256), so an instance's slots are evenly
+// spaced and one strided reduction observes them all.
+// ------------------------------------------------------------------------------------------
+
+static chfpe_status ensure_partial(chfpe_handle *h, int cap) {
+    if (h->partial_cap >= cap) return CHFPE_OK;
+    chfpe_status st = CHFPE_OK;
+    double *p = dalloc<double>((size_t)cap, &st);
+    if (st) return st;
+    if (h->partial) cudaFree(h->partial);
+    h->partial = p;
+    h->partial_cap = cap;
+    return CHFPE_OK;
+}
+
+static chfpe_status build_branches(chfpe_handle *b, int cap) {
+    if (b->branches && b->branch_cap == cap) return CHFPE_OK;
+    chfpe_destroy(b->branches);
+    b->branches = nullptr;
+    b->branch_cap = 0;
+    const int n = (int)b->inst.size();
+    chfpe_handle *bb = new chfpe_handle();
+    bb->model = b->model;
+    bb->grid = b->grid;
+    bb->opts = b->opts;
+    bb->d = b->d;
+    bb->depth = b->depth;
+    bb->M = b->M;
+    bb->M32 = b->M32;
+    bb->prec = b->prec;
+    bb->esize = b->esize;
+    bb->nsub = b->nsub;
+    bb->dt = b->dt;
+    bb->stream = b->stream;
+    bb->own_stream = false;
+    bb->inst_borrowed = true;
+    b->branch_base.assign(n, 0);
+    b->branch_pitch.assign(n, 0);
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        chfpe_handle *c = b->inst[i];
+        b->branch_pitch[i] = (c->state_bytes + 255) / 256 * 256;
+        b->branch_base[i] = total;
+        for (int s = 0; s < cap; ++s) {
+            bb->inst.push_back(c);
+            bb->inst_off.push_back(total + s * b->branch_pitch[i]);
+            bb->cells_total += (double)c->state;
+        }
+        total += cap * b->branch_pitch[i];
+    }
+    chfpe_status st = CHFPE_OK;
+    void **arenas[] = {&bb->cy, &bb->ca, &bb->cb};
+    for (void **p : arenas) if (!st) *p = (void *)dalloc<char>((size_t)total, &st);
+    if (!st) CK(cudaMemsetAsync(bb->cy, 0, (size_t)total, bb->stream));
+    for (int i = 0; i < n && !st; ++i)
+        st = ensure_partial(b->inst[i], observe_blocks(b->inst[i]) * cap);
+    if (!st) st = b->prec == 64 ? batch_setup_geo<double>(bb) : batch_setup_geo<float>(bb);
+    if (st) { chfpe_destroy(bb); return st; }
+    bb->launches = 0;
+    b->branches = bb;
+    b->branch_cap = cap;
+    return CHFPE_OK;
+}
+
+extern "C" chfpe_status chfpe_batch_response2(chfpe_handle *b, const chfpe_optical *A,
+                                              const chfpe_optical *B, const chfpe_optical *C,
+                                              int nt1, int nt2, int stride, double *R) {
+    if (!b || b->inst.empty() || !A || !B || !C || !R)
+        return fail(CHFPE_EINVAL, "null argument or not a batch");
+    if (nt1 < 1 || nt2 < 1 || stride < 0) return fail(CHFPE_EINVAL, "nt1, nt2 >= 1, stride >= 0");
+    const int n = (int)b->inst.size();
+    chfpe_status st;
+    for (int i = 0; i < n; ++i)
+        if (!b->inst[i]->have_eq) return fail(CHFPE_ESTATE, "instance " + std::to_string(i) + " has no equilibrium");
+    const int cap = std::min(nt1, std::max(1, b->opts.max_batch));
+    if ((st = build_branches(b, cap))) return st;
+    chfpe_handle *bb = b->branches;
+    const size_t per = (size_t)nt1 * nt2;
+    if ((st = ensure_dR(b, (size_t)n * per))) return st;
+    for (int i = 0; i < n; ++i) {
+        chfpe_handle *c = b->inst[i];
+        if ((st = set_observable(c, C))) return st;
+        if ((st = insert(c, A, c->eq, 0, c->cy, 1))) return st;     // chain = A^x W_eq
+    }
+    const long steps = (long)stride * b->nsub;
+    auto advance = [&](chfpe_handle *h) -> chfpe_status {
+        return h->prec == 64 ? batch_rk4<double>(h, steps) : batch_rk4<float>(h, steps);
+    };
+    const double cells0 = bb->cell_updates;
+    const long long launches0 = bb->launches;
+    for (int i0 = 0; i0 < nt1; i0 += cap) {
+        const int nb = std::min(cap, nt1 - i0);
+        // spawn branch i0 + s of every instance along its chain: slot s = B^x chain(t1)
+        for (int s = 0; s < nb; ++s) {
+            for (int i = 0; i < n; ++i) {
+                chfpe_handle *c = b->inst[i];
+                char *slot = (char *)bb->cy + b->branch_base[i] + s * b->branch_pitch[i];
+                if ((st = insert(c, B, c->cy, 0, slot, 1))) return st;
+            }
+            if (i0 + s + 1 < nt1 && (st = advance(b))) return st;
+        }
+        // every instance's slots advance together; slots beyond nb (last chunk) ride along
+        for (int k = 0; k < nt2; ++k) {
+            if (k > 0 && (st = advance(bb))) return st;
+            for (int i = 0; i < n; ++i) {
+                chfpe_handle *c = b->inst[i];
+                const char *first = (const char *)bb->cy + b->branch_base[i];
+                double *out = b->dR + (size_t)i * per + (size_t)i0 * nt2 + k;
+                if ((st = observe(c, first, nb, out, nt2, nullptr, b->branch_pitch[i]))) return st;
+            }
+        }
+    }
+    b->cell_updates += bb->cell_updates - cells0;
+    b->launches += bb->launches - launches0;
+    for (int i = 0; i < n; ++i) b->inst[i]->have_state = true;
+    return finish_response(b, R, (size_t)n * per);
 }

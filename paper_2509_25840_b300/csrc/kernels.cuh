@@ -52,7 +52,9 @@ struct MemberTable {
     int n[M][3];
     int up[M][3];   // index of n + e_s, or -1
     int dn[M][3];   // index of n - e_s, or -1
-    constexpr MemberTable() : n{}, up{}, dn{} {
+    int last[M];    // the last member (in processing order) that adds to member i's right-hand
+                    // side: i itself or its highest up-neighbour
+    constexpr MemberTable() : n{}, up{}, dn{}, last{} {
         int c = 0;
         for (int t = 0; t <= DEPTH; ++t) {
             if (D == 1) {
@@ -83,6 +85,11 @@ struct MemberTable {
                     if (isdn) dn[i][s] = j;
                 }
             }
+        for (int i = 0; i < M; ++i) {
+            last[i] = i;
+            for (int s = 0; s < 3; ++s)
+                if (up[i][s] > last[i]) last[i] = up[i][s];
+        }
     }
 };
 
@@ -337,7 +344,11 @@ __device__ __forceinline__ void prefetch_member(const S *g, const Geo<T> &a, int
 // vectors of member m + 1 into its own shared-memory slots by cp.async while member m is
 // computed (two slot sets, 6 D float4 each; the thread reads only what it copied itself, so
 // cp.async.wait_group orders everything and no block barrier is needed)
-template <typename T, int D, int DEPTH, int V, int M32, bool NC = true, bool PF = false, int QS = 0>
+// ES = true (early stores): member i's result is written as soon as the last member adding to it
+// (MemberTable::last) has been processed, instead of after the whole hierarchy -- the same values,
+// with fewer accumulators live at once.
+template <typename T, int D, int DEPTH, int V, int M32, bool NC = true, bool PF = false, int QS = 0,
+          bool ES = false>
 __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, const char *y,
                                              char *out, T c, int x0) {
     constexpr MemberTable<D, DEPTH> tab{};
@@ -378,6 +389,27 @@ __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, co
     for (int m = 0; m < M; ++m)
 #pragma unroll
         for (int j = 0; j < V; ++j) acc[m][j] = T(0);
+
+    // out^(m) = y^(m) + c acc^(m)   (or c acc^(m) without a base state)
+    auto store_member = [&](int m) {
+        T r[V];
+        if (y) {
+            T yv[V];
+            if (m < M32)
+                vload_rw<T, V>(member_t<T, M32>(y, m, a.P) + x0, yv);
+            else
+                vload_rw<T, V>(member_h<T, M32>(y, m, a.P) + x0, yv);
+#pragma unroll
+            for (int j = 0; j < V; ++j) r[j] = yv[j] + c * acc[m][j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) r[j] = c * acc[m][j];
+        }
+        if (m < M32)
+            vstore<T, V>(const_cast<T *>(member_t<T, M32>(out, m, a.P)) + x0, r);
+        else
+            vstore<T, V>(const_cast<bf16 *>(member_h<T, M32>(out, m, a.P)) + x0, r);
+    };
 
     auto q_issue = [&](int mm, int buf) {   // member mm's q-neighbours into slot set buf
         const T *g = member_t<T, M32>(in, mm, a.P);
@@ -436,37 +468,63 @@ __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, co
                 }
             }
         }
+        if constexpr (ES) {
+#pragma unroll
+            for (int i = 0; i < M; ++i)
+                if (tab.last[i] == m) store_member(i);
+        }
     }
 
+    if constexpr (!ES) {
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-        T r[V];
-        if (y) {
-            T yv[V];
-            if (m < M32)
-                vload_rw<T, V>(member_t<T, M32>(y, m, a.P) + x0, yv);
-            else
-                vload_rw<T, V>(member_h<T, M32>(y, m, a.P) + x0, yv);
-#pragma unroll
-            for (int j = 0; j < V; ++j) r[j] = yv[j] + c * acc[m][j];
-        } else {
-#pragma unroll
-            for (int j = 0; j < V; ++j) r[j] = c * acc[m][j];
-        }
-        if (m < M32)
-            vstore<T, V>(const_cast<T *>(member_t<T, M32>(out, m, a.P)) + x0, r);
-        else
-            vstore<T, V>(const_cast<bf16 *>(member_h<T, M32>(out, m, a.P)) + x0, r);
+        for (int m = 0; m < M; ++m) store_member(m);
     }
 }
 
 template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32, bool PF = false,
-          bool QST = false>
+          bool QST = false, bool ES = false>
 __global__ void __launch_bounds__(NT, MINB) stage_vec_kernel(const StageArgs<T> a) {
     const int x0 = (blockIdx.x * NT + threadIdx.x) * V;
     if (x0 >= a.g.P) return;
     const long long boff = (long long)blockIdx.y * a.state_bytes;
-    stage_points<T, D, DEPTH, V, M32, true, PF, QST ? NT : 0>(
+    stage_points<T, D, DEPTH, V, M32, true, PF, QST ? NT : 0, ES>(
+        a.g, a.in + boff, a.y ? a.y + boff : nullptr, a.out + boff, a.c, x0);
+}
+
+// ------------------------------------------------------------------------------------------
+// the same stage with a tiled block -> row mapping.  A "row" is one line of the fastest axis
+// p_d (every axis but p_d fixed); tpr = n_pd / V threads cover a row.  Each block covers a box of
+// B[0] x .. x B[2d-2] rows (B = 1 on axes not tiled), so that the stencil taps of one thread
+// along a tiled axis are, for the interior of the box, points another thread of the block
+// loads too (L1 hits instead of L2 round trips).  Boxes are numbered with the last row axis
+// fastest; a box that sticks out of the grid leaves its outside threads idle.
+// ------------------------------------------------------------------------------------------
+
+struct RowTile {
+    int B[5];       // box extent per row axis (q_1..q_d, p_1..p_{d-1})
+    int nb[5];      // boxes per row axis: ceil(n / B)
+    int tpr;        // threads per row (n_pd / V)
+    int rows;       // rows per box (product of B)
+};
+
+template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32, bool ES = false>
+__global__ void __launch_bounds__(NT, MINB) stage_tile_kernel(const StageArgs<T> a, const RowTile t) {
+    constexpr int NR = 2 * D - 1;
+    int lr = threadIdx.x / t.tpr;              // row inside the box
+    if (lr >= t.rows) return;
+    const int lane = threadIdx.x - lr * t.tpr;
+    int b = blockIdx.x;
+    int x0 = lane * V;
+#pragma unroll
+    for (int ax = NR - 1; ax >= 0; --ax) {
+        const int c = (b % t.nb[ax]) * t.B[ax] + lr % t.B[ax];
+        b /= t.nb[ax];
+        lr /= t.B[ax];
+        if (c >= a.g.n[ax]) return;
+        x0 += c * a.g.st[ax];
+    }
+    const long long boff = (long long)blockIdx.y * a.state_bytes;
+    stage_points<T, D, DEPTH, V, M32, true, false, 0, ES>(
         a.g, a.in + boff, a.y ? a.y + boff : nullptr, a.out + boff, a.c, x0);
 }
 

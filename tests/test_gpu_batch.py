@@ -163,3 +163,142 @@ def test_batch_tilings_of_the_multiple_of_4_class_agree(monkeypatch):
     for i in range(len(insts)):
         scale = np.abs(out["0"][i]).max()
         assert np.abs(out["0"][i] - out["3"][i]).max() <= 1e-6 * scale
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_batch_response2_matches_single_handles_and_oracle(prec):
+    """chfpe_batch_response2 (every instance's branches advanced by the same launches, 2 t1 rows
+    per chunk so that the last chunk is partial) against single handles and the FP64 oracle per
+    instance (Eq. 2Dresponse): FP64 1e-10, FP32 1e-4 of max|R2|; the three instances cover the
+    4-, 2- and 1-point work lists."""
+    chfpe = _chfpe()
+    insts = _instances()
+    depth, dt, nt1, nt2, stride = 2, 0.004, 5, 4, 5
+    A = inputs.Optical(lin=(1.0, 0.7), quad=[[0.2, 0.1], [0.1, -0.1]])
+    Bo = inputs.Optical(lin=(0.5, 1.0), quad=[[-0.3, 0.0], [0.0, 0.4]])
+    with chfpe.Batch([m for m, _ in insts], [g for _, g in insts], depth=depth, dt=dt,
+                     precision=prec, max_batch=2) as b:
+        for i, (m, g) in enumerate(insts):
+            b.instance(i).set_equilibrium(_eq(m, g, depth))
+        R = b.response2_all(A, Bo, A, nt1, nt2, stride)
+        again = b.response2_all(A, Bo, A, nt1, nt2, stride)      # arenas kept, same result
+    assert np.array_equal(R, again)
+    for i, (m, g) in enumerate(insts):
+        W = _eq(m, g, depth)
+        with chfpe.Handle(m, g, depth=depth, dt=dt, precision=prec, max_batch=3) as h:
+            h.set_equilibrium(W)
+            single = h.response2(A, Bo, A, nt1, nt2, stride)
+        scale = np.abs(single).max()
+        assert np.abs(R[i] - single).max() <= (1e-13 if prec == 64 else 1e-6) * scale
+        pb = oracle.Problem(m, g, depth)
+        Wr = W if prec == 64 else W.astype(np.float32).astype(np.float64)
+        want = oracle.response2(pb, A, Bo, A, Wr, dt, nt1, nt2, stride)
+        tol = 1e-10 if prec == 64 else 1e-4
+        assert np.abs(R[i] - want).max() <= tol * np.abs(want).max(), (i, prec)
+
+
+def _max_dt(model, grid, depth):
+    """The largest dt a single handle accepts (its RK4 stability check), by bisection."""
+    chfpe = _chfpe()
+    lo, hi = 1e-6, 1.0
+    for _ in range(40):
+        mid = (lo * hi) ** 0.5
+        try:
+            chfpe.Handle(model, grid, depth=depth, dt=mid, precision=64, max_batch=0).close()
+            lo = mid
+        except chfpe.ChfpeError:
+            hi = mid
+    return lo
+
+
+def _three_periods(depth):
+    """Three instances whose substeps in one batch are 1, 2 and 4 (stiffness from gamma)."""
+    (m0, g0), _, (m2, g2) = _instances()
+    dt = 0.98 * _max_dt(m0, g0, depth)
+    picked = [(m0, g0, 1)]
+    for want, lo, hi in ((2, 0.52, 0.95), (4, 0.27, 0.47)):
+        for gam in np.geomspace(1.0, 400.0, 60):
+            m = m2.replace(gamma=(float(gam), float(gam)), zeta=(1.0, 1.0))
+            r = _max_dt(m, g2, depth) / dt
+            if lo < r < hi:
+                picked.append((m, g2, want))
+                break
+    assert [k for _, _, k in picked] == [1, 2, 4], "no gamma gave the wanted substep"
+    return dt, picked
+
+
+def test_batch_mixed_substep_levels_match_single_handles_and_oracle():
+    """Instances substepping 1, 2 and 4 times per nominal step in one batch: each against a
+    single handle stepping its own dt / k (FP64, 1e-13 of max) for R1 and R2, and the FP32
+    batch against the FP64 oracle at the instance's own step (1e-4)."""
+    chfpe = _chfpe()
+    depth, nt, stride = 2, 4, 3
+    dt, picked = _three_periods(depth)
+    mu = inputs.Optical(lin=(1.0, 1.0), quad=[[0.1, 0.0], [0.0, 0.2]])
+    models, grids = [m for m, _, _ in picked], [g for _, g, _ in picked]
+    R = {}
+    for prec in (64, 32):
+        with chfpe.Batch(models, grids, depth=depth, dt=dt, precision=prec, max_batch=2) as b:
+            for i, (m, g, _) in enumerate(picked):
+                b.instance(i).set_equilibrium(_eq(m, g, depth))
+            R[prec] = (b.response1_all(mu, mu, nt, stride),
+                       b.response2_all(mu, mu, mu, nt, nt, stride))
+    for i, (m, g, k) in enumerate(picked):
+        W = _eq(m, g, depth)
+        with chfpe.Handle(m, g, depth=depth, dt=dt / k, precision=64, max_batch=nt) as h:
+            h.set_equilibrium(W)
+            r1 = h.response1(mu, mu, nt, stride * k)
+            r2 = h.response2(mu, mu, mu, nt, nt, stride * k)
+        assert np.abs(R[64][0][i] - r1).max() <= 1e-13 * np.abs(r1).max(), i
+        assert np.abs(R[64][1][i] - r2).max() <= 1e-13 * np.abs(r2).max(), i
+        pb = oracle.Problem(m, g, depth)
+        Wr = W.astype(np.float32).astype(np.float64)
+        want1 = oracle.response1(pb, mu, mu, Wr, dt / k, nt, stride * k)
+        assert np.abs(R[32][0][i] - want1).max() <= 1e-4 * np.abs(want1).max(), i
+
+
+def test_batch_response2_with_bf16_tiers_vs_fp64_oracle():
+    """Two-mode depth-4 instances with tiers 3-4 stored as bf16 (FP32 compute): the batched R2
+    against the FP64 oracle is held to the FP32 bar (1e-4 of max|R2|)."""
+    chfpe = _chfpe()
+    model = inputs.two_mode_model()
+    grids = [inputs.default_grid(model, [12, 12, 12, 12]), inputs.default_grid(model, [12, 13, 12, 14])]
+    depth, dt, nt, stride = 4, 0.005, 3, 40
+    mu = inputs.Optical(lin=(1.0, 1.0))
+    with chfpe.Batch([model, model], grids, depth=depth, dt=dt, precision=32, bf16_tier=3,
+                     max_batch=3) as b:
+        Ws = [_eq(model, g, depth) for g in grids]
+        for i, W in enumerate(Ws):
+            b.instance(i).set_equilibrium(W)
+        R = b.response2_all(mu, mu, mu, nt, nt, stride)
+    for i, g in enumerate(grids):
+        pb = oracle.Problem(model, g, depth)
+        want = oracle.response2(pb, mu, mu, mu, Ws[i], dt, nt, nt, stride)
+        err = np.abs(R[i] - want).max() / np.abs(want).max()
+        print(f"bf16 tiers, batched R2, instance {i}: normalised error vs FP64 oracle {err:.2e}")
+        assert err < 1e-4
+
+
+def test_borrowed_instances_step_their_own_dt():
+    """A borrowed instance counts steps of its own dt_i = dt / nsub_i (chfpe_time_step): two
+    instances of different substeps propagated through their borrowed handles equal single handles
+    at dt_i for the same step count (FP64, 1e-13 of max)."""
+    chfpe = _chfpe()
+    depth = 2
+    dt, picked = _three_periods(depth)
+    picked = [picked[0], picked[2]]                     # substeps 1 and 4
+    with chfpe.Batch([m for m, _, _ in picked], [g for _, g, _ in picked], depth=depth, dt=dt,
+                     precision=64) as b:
+        assert b.time_step() == pytest.approx(dt / 4, rel=1e-15)
+        for i, (m, g, k) in enumerate(picked):
+            inst = b.instance(i)
+            assert inst.time_step() == pytest.approx(dt / k, rel=1e-15)
+            W = inputs.random_state(g, inst.members, seed=60 + i, smooth=True)
+            inst.set_state(W)
+            inst.propagate(6)
+            got = inst.get_state()
+            with chfpe.Handle(m, g, depth=depth, dt=dt / k, precision=64) as h:
+                h.set_state(W)
+                h.propagate(6)
+                want = h.get_state()
+            assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
