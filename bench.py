@@ -41,9 +41,12 @@ from paper_2509_25840_b300 import inputs  # noqa: E402
 
 ELEM_ACCESSES_PER_CELL_STEP = 11      # Horner-form RK4: 2 + 3 + 3 + 3 element accesses
 ELEM_ACCESSES_TEXTBOOK = 16           # the three-array k1..k4 form: 3 + 5 + 5 + 3
+# launch shapes of the RK4 stage kernel the library's autotuner chooses from (variant index ->
+# points per thread, threads per block, minimum resident blocks per SM), as in stage_launch.cuh
 STAGE_SHAPES = {0: (2, 128, 8), 1: (2, 256, 4), 2: (2, 128, 6), 3: (4, 128, 4), 4: (4, 128, 4), 5: (4, 128, 4),
                 6: (4, 256, 2), 7: (4, 64, 8), 8: (4, 128, 4),
-                9: (4, 128, 4), 10: (4, 128, 3), 11: (4, 128, 2)}
+                9: (4, 128, 4), 10: (4, 128, 3), 11: (4, 128, 2), 12: (4, 128, 4), 13: (4, 128, 4),
+                14: (4, 128, 4), 15: (4, 256, 2), 16: (4, 128, 4), 17: (4, 128, 4)}
 
 
 def parse():
@@ -254,13 +257,18 @@ def spawn_branches(h, wl, nt1, torch, dev):
 
 
 def stage_kernel_name(variant: int, M: int = 15) -> str:
+    """The chosen shape's kernel as ncu names it (template arguments of the two-mode, depth-4
+    instantiation)."""
     V, NT, MINB = STAGE_SHAPES[variant]
+    b = lambda x: "true" if x else "false"
     if variant == 4:
-        return "stage_bulk_kernel<4,128>"
+        return "stage_bulk_kernel<4, 128>"
     if variant == 5:
-        return "stage_cpasync_kernel<4,128>"
-    return "stage_vec_kernel<float,2,4,%d,%d,%d,%d,%d,%d>" % (V, NT, MINB, M, int(variant == 8),
-                                                               int(variant == 9))
+        return "stage_cpasync_kernel<4, 128>"
+    if variant in (12, 13, 14, 15, 17):
+        return "stage_tile_kernel<float, 2, 4, 4, %d, %d, %d, %s>" % (NT, MINB, M, b(variant == 17))
+    return "stage_vec_kernel<float, 2, 4, %d, %d, %d, %d, %s, %s, %s>" % (
+        V, NT, MINB, M, b(variant == 8), b(variant == 9), b(variant == 16))
 
 
 def run_ours(args, rank, world, local, pg):

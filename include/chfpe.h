@@ -134,6 +134,16 @@ chfpe_status chfpe_response1(chfpe_handle *h, const chfpe_optical *A, const chfp
 chfpe_status chfpe_response2(chfpe_handle *h, const chfpe_optical *A, const chfpe_optical *B,
                              const chfpe_optical *C, int nt1, int nt2, int stride, double *R);
 
+/* R3 (Eq. 3Dresponse) at one waiting time t2 = n2 dt, the third-order (2D IR) signal of
+ * Sec. IV C: R[i*nt3 + j] = integral D G(j stride dt) C^x G(n2 dt) B^x G(i stride dt) A^x W_eq,
+ * i = 0..nt1-1 (t1), j = 0..nt3-1 (t3), into caller-owned host memory (nt1*nt3 doubles).  The
+ * t1 branches of a chunk of up to max_batch branches advance together through the waiting time
+ * and the t3 sampling (one batched launch per RK4 stage).  chfpe_spectrum3 turns R into
+ * I(w3, t2, w1) (Eq. noncorrelation). */
+chfpe_status chfpe_response3(chfpe_handle *h, const chfpe_optical *A, const chfpe_optical *B,
+                             const chfpe_optical *C, const chfpe_optical *D, int nt1, long n2,
+                             int nt3, int stride, double *R);
+
 /* Save / load the equilibrium (FP64, with a header: grid, depth, members) -- Sec. IV B saves
  * W_eq to a file and Sec. IV C reads it back. */
 chfpe_status chfpe_save_equilibrium(const chfpe_handle *h, const char *path);
@@ -180,6 +190,28 @@ chfpe_status chfpe_batch_response1(chfpe_handle *batch, const chfpe_optical *A,
 chfpe_status chfpe_batch_response2(chfpe_handle *batch, const chfpe_optical *A,
                                    const chfpe_optical *B, const chfpe_optical *C, int nt1,
                                    int nt2, int stride, double *R);
+
+/* ---- spectra from sampled responses (Sec. II C) ------------------------------------------------
+ *
+ * A response sampled at t_k = k dtau, k = 0..N-1, stands for the integral over [0, (N-1) dtau] by
+ * the trapezoid rule (weights dtau, halved at both ends) with an optional window exp(-eta t)
+ * (eta >= 0; 0 = none) and zero beyond the last sample.  Output frequencies are the centred grid
+ * w_j = 2 pi (j - L/2) / (L dtau), j = 0..L-1 (w = 0 at j = L/2; L >= N zero-pads).  Each sign is
+ * the one its equation prints.  Host arrays in and out (caller-owned); the transform runs as an
+ * FP64 direct DFT on the GPU (a few temporary device buffers, freed before return), on `stream`
+ * (a cudaStream_t, or NULL) and synchronously.  CHFPE_EINVAL for N < 2, L < N, L > 2^22,
+ * dtau <= 0 or eta < 0; CHFPE_ECUDA. */
+/* Eq. 1DIR_Raman: I[j] = w_j Im sum_k c_k e^{+i w_j t_k} R1[k]   (R1 as from chfpe_response1). */
+chfpe_status chfpe_spectrum1(const double *R1, int nt, double dtau, int L, double eta, double *I,
+                             void *stream);
+/* Eq. 2DThz_Raman: I[a][b] = Im sum_{k1,k2} c_k1 c_k2 e^{-i w_a t_k1 - i w_b t_k2} R2[k1][k2]
+ * (R2[t1][t2] as from chfpe_response2; a indexes w1 on the L1 grid, b indexes w2 on the L2 grid). */
+chfpe_status chfpe_spectrum2(const double *R2, int nt1, int nt2, double dtau, int L1, int L2,
+                             double eta, double *I, void *stream);
+/* Eq. noncorrelation at one t2: I[a][b] = Im sum c_k1 c_k3 e^{-i w_a t_k1 + i w_b t_k3} R3[k1][k3]
+ * (R3[t1][t3] as from chfpe_response3; a indexes w1, b indexes w3). */
+chfpe_status chfpe_spectrum3(const double *R3, int nt1, int nt3, double dtau, int L1, int L3,
+                             double eta, double *I, void *stream);
 
 /* Sizes of the handle: members M and points per member P (states are M*P values). */
 chfpe_status chfpe_sizes(const chfpe_handle *h, int *members, long *points);

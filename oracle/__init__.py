@@ -24,6 +24,8 @@ Parity status per function (what pins it; the pins live in ``tests/test_oracle_p
   observe      Gaussian moments of the sampled Boltzmann distribution
   equilibrate  stationarity of its result; agreement with the sampled Boltzmann to O(h^6)
   response1/2  closed forms and moment closure above
+  response3    the moment closure (one mode, deep hierarchy, linear and quadratic optics) and
+               the vanishing third-order response of the harmonic / all-linear case
 """
 from __future__ import annotations
 
@@ -297,4 +299,24 @@ def response2(pb: Problem, A, B, C, Weq, dt: float, nt1: int, nt2: int, stride: 
     if _load().orc_response2(pb._ptr(), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                              _p(Weq), float(dt), int(nt1), int(nt2), int(stride), _p(R)):
         raise RuntimeError("orc_response2 failed")
+    return R
+
+
+def response3(pb: Problem, A, B, C, D, Weq, dt: float, nt1: int, n2: int, nt3: int,
+              stride: int) -> np.ndarray:
+    """Eq. 3Dresponse at one waiting time t2 = n2 dt:
+    R[a][c] = integral D G(c stride dt) C^x G(n2 dt) B^x G(a stride dt) A^x W_eq,
+    a = 0..nt1-1 (t1), c = 0..nt3-1 (t3); each t1 branch propagated on its own, in the order
+    the equation applies its operators (insert, rk4 and observe are the C oracle's)."""
+    W = insert(pb, A, _as_state(pb, Weq))
+    R = np.zeros((nt1, nt3))
+    for a in range(nt1):
+        X = rk4(pb, insert(pb, B, W), dt, n2)
+        X = insert(pb, C, X)
+        for c in range(nt3):
+            R[a, c] = observe(pb, D, X)
+            if c + 1 < nt3:
+                X = rk4(pb, X, dt, stride)
+        if a + 1 < nt1:
+            W = rk4(pb, W, dt, stride)
     return R

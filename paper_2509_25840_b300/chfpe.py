@@ -94,6 +94,9 @@ def load(path: str = LIB_PATH):
         "chfpe_response2": ([_H, ctypes.POINTER(chfpe_optical), ctypes.POINTER(chfpe_optical),
                              ctypes.POINTER(chfpe_optical), ctypes.c_int, ctypes.c_int,
                              ctypes.c_int, _DP], S),
+        "chfpe_response3": ([_H, ctypes.POINTER(chfpe_optical), ctypes.POINTER(chfpe_optical),
+                             ctypes.POINTER(chfpe_optical), ctypes.POINTER(chfpe_optical),
+                             ctypes.c_int, ctypes.c_long, ctypes.c_int, ctypes.c_int, _DP], S),
         "chfpe_save_equilibrium": ([_H, ctypes.c_char_p], S),
         "chfpe_load_equilibrium": ([_H, ctypes.c_char_p], S),
         "chfpe_sizes": ([_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)], S),
@@ -116,6 +119,12 @@ def load(path: str = LIB_PATH):
         "chfpe_batch_response2": ([_H, ctypes.POINTER(chfpe_optical), ctypes.POINTER(chfpe_optical),
                                    ctypes.POINTER(chfpe_optical), ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, _DP], S),
+        "chfpe_spectrum1": ([_DP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                             _DP, _VP], S),
+        "chfpe_spectrum2": ([_DP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                             ctypes.c_int, ctypes.c_double, _DP, _VP], S),
+        "chfpe_spectrum3": ([_DP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                             ctypes.c_int, ctypes.c_double, _DP, _VP], S),
         "chfpe_stats_reset": ([_H, ctypes.c_int], S),
         "chfpe_stats_get": ([_H, ctypes.POINTER(chfpe_stats)], S),
         "chfpe_last_error": ([], ctypes.c_char_p),
@@ -203,6 +212,40 @@ def observe_noalloc(model, grid, depth: int, precision: int, C, states_ptr: int,
     _check(load().chfpe_observe_noalloc(ctypes.byref(m), ctypes.byref(g), int(depth),
                                         int(precision), ctypes.byref(c), states_ptr, int(batch),
                                         R_ptr, stream))
+
+
+def frequencies(L: int, dtau: float) -> np.ndarray:
+    """The centred frequency grid of the spectra: w_j = 2 pi (j - L/2) / (L dtau)."""
+    return 2.0 * np.pi * (np.arange(L) - L // 2) / (L * dtau)
+
+
+def spectrum1(R1, dtau: float, L: int, eta: float = 0.0, stream: int | None = None) -> np.ndarray:
+    """chfpe_spectrum1 (Eq. 1DIR_Raman): I[j] on frequencies(L, dtau)."""
+    R = np.ascontiguousarray(R1, dtype=np.float64)
+    out = np.empty(int(L))
+    _check(load().chfpe_spectrum1(_dptr(R), R.shape[0], float(dtau), int(L), float(eta),
+                                  _dptr(out), stream))
+    return out
+
+
+def spectrum2(R2, dtau: float, L1: int, L2: int, eta: float = 0.0,
+              stream: int | None = None) -> np.ndarray:
+    """chfpe_spectrum2 (Eq. 2DThz_Raman): I[w1][w2] from R2[t1][t2]."""
+    R = np.ascontiguousarray(R2, dtype=np.float64)
+    out = np.empty((int(L1), int(L2)))
+    _check(load().chfpe_spectrum2(_dptr(R), R.shape[0], R.shape[1], float(dtau), int(L1), int(L2),
+                                  float(eta), _dptr(out), stream))
+    return out
+
+
+def spectrum3(R3, dtau: float, L1: int, L3: int, eta: float = 0.0,
+              stream: int | None = None) -> np.ndarray:
+    """chfpe_spectrum3 (Eq. noncorrelation at one t2): I[w1][w3] from R3[t1][t3]."""
+    R = np.ascontiguousarray(R3, dtype=np.float64)
+    out = np.empty((int(L1), int(L3)))
+    _check(load().chfpe_spectrum3(_dptr(R), R.shape[0], R.shape[1], float(dtau), int(L1), int(L3),
+                                  float(eta), _dptr(out), stream))
+    return out
 
 
 class Handle:
@@ -322,6 +365,16 @@ class Handle:
         a, b, c = make_optical(A), make_optical(B), make_optical(C)
         _check(load().chfpe_response2(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                       int(nt1), int(nt2), int(stride), _dptr(R)))
+        return R
+
+    def response3(self, A, B, C, D, nt1: int, n2: int, nt3: int, stride: int,
+                  out: np.ndarray | None = None) -> np.ndarray:
+        """chfpe_response3 (Eq. 3Dresponse) at waiting time n2 dt: R[t1][t3]."""
+        R = np.empty((nt1, nt3)) if out is None else out
+        a, b, c, d = make_optical(A), make_optical(B), make_optical(C), make_optical(D)
+        _check(load().chfpe_response3(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                      ctypes.byref(d), int(nt1), int(n2), int(nt3), int(stride),
+                                      _dptr(R)))
         return R
 
     def stage_tuning(self):

@@ -1208,6 +1208,42 @@ extern "C" chfpe_status chfpe_response2(chfpe_handle *h, const chfpe_optical *A,
     return finish_response(h, R, total);
 }
 
+// Eq. 3Dresponse at one waiting time t2 = n2 dt (the 2D IR / third-order signal of Sec. IV C):
+// the t1 chain A^x W_eq spawns branch i = B^x chain(t1 = i stride dt) into batch slot c; a chunk
+// of branches advances n2 RK4 steps together, takes C^x (batched insertion into the second
+// branch arena) and is then sampled along t3 by the same dispatch as R2's branch phase.
+extern "C" chfpe_status chfpe_response3(chfpe_handle *h, const chfpe_optical *A,
+                                        const chfpe_optical *B, const chfpe_optical *C,
+                                        const chfpe_optical *D, int nt1, long n2, int nt3,
+                                        int stride, double *R) {
+    if (!h || !A || !B || !C || !D || !R) return fail(CHFPE_EINVAL, "null argument");
+    if (nt1 < 1 || nt3 < 1 || n2 < 0 || stride < 0)
+        return fail(CHFPE_EINVAL, "nt1, nt3 >= 1, n2 >= 0, stride >= 0");
+    if (!h->have_eq) return fail(CHFPE_ESTATE, "no equilibrium: call chfpe_equilibrate or chfpe_set_equilibrium");
+    if (h->opts.max_batch < 1) return fail(CHFPE_EINVAL, "handle created with max_batch = 0: no branch arenas");
+    chfpe_status st;
+    const size_t total = (size_t)nt1 * nt3;
+    if ((st = ensure_dR(h, total))) return st;
+    if ((st = set_observable(h, D))) return st;
+    if ((st = insert(h, A, h->eq, 0, h->cy, 1))) return st;
+    const int cap = h->opts.max_batch;
+    const size_t sbytes = (size_t)h->state_bytes;
+    for (int i0 = 0; i0 < nt1; i0 += cap) {
+        const int nb = std::min(cap, nt1 - i0);
+        for (int c = 0; c < nb; ++c) {
+            if ((st = insert(h, B, h->cy, 0, (char *)h->by + c * sbytes, 1))) return st;
+            if (i0 + c + 1 < nt1 && (st = rk4_any(h, h->cy, h->ca, h->cb, 1, stride))) return st;
+        }
+        if ((st = rk4_any(h, h->by, h->ba, h->bb, nb, n2))) return st;          // waiting time
+        if ((st = insert(h, C, h->by, h->state_bytes, h->ba, nb))) return st;  // C^x, batched
+        if ((st = sampled_propagation(h, h->ba, h->by, h->bb, nb, nt3, stride,
+                                      h->dR + (size_t)i0 * nt3, nt3)))
+            return st;
+    }
+    h->have_state = true;
+    return finish_response(h, R, total);
+}
+
 // ------------------------------------------------------------------------------------------
 // device-buffer entry points
 // ------------------------------------------------------------------------------------------

@@ -312,6 +312,28 @@ class MomentClosure:
         return R
 
 
+    def response3(self, A, B, C, D, W0, grid, dt, nt1, n2, nt3, stride):
+        """Eq. 3Dresponse at one waiting time n2 dt: R[a][c] with t1 = a stride dt and
+        t3 = c stride dt, from the adjoint chain D <- (C^x)' <- G(n2) <- (B^x)' <- G(t1) <- (A^x)'."""
+        P = np.linalg.matrix_power(rk4_poly(dt * self.M), stride)
+        P2 = np.linalg.matrix_power(rk4_poly(dt * self.M), n2)
+        Ax, Bx, Cx = self.insertion(A), self.insertion(B), self.insertion(C)
+        meq = self.equilibrium_moments(W0, grid)
+        row = meq @ Ax
+        rows = []
+        for _ in range(nt1):
+            rows.append(row)
+            row = row @ P
+        f = self.observable(D)
+        R = np.zeros((nt1, nt3))
+        for c in range(nt3):
+            h = Bx @ (P2 @ (Cx @ f))
+            for a in range(nt1):
+                R[a, c] = rows[a] @ h
+            f = P @ f
+        return R
+
+
 # ------------------------------------------------------------------------------------------
 # classical trajectories (zeta = 0)
 # ------------------------------------------------------------------------------------------

@@ -259,11 +259,13 @@ def test_batch_mixed_substep_levels_match_single_handles_and_oracle():
 
 def test_batch_response2_with_bf16_tiers_vs_fp64_oracle():
     """Two-mode depth-4 instances with tiers 3-4 stored as bf16 (FP32 compute): the batched R2
-    against the FP64 oracle is held to the FP32 bar (1e-4 of max|R2|)."""
+    against the FP64 oracle is held to the FP32 bar (1e-4 of max|R2|) over t1, t2 <= 1.2 (over
+    t <= 0.4 alone R2 has not developed, and FP32 rounding of the O(1) branch states shows at
+    1e-4 of that small maximum with or without bf16 tiers)."""
     chfpe = _chfpe()
     model = inputs.two_mode_model()
     grids = [inputs.default_grid(model, [12, 12, 12, 12]), inputs.default_grid(model, [12, 13, 12, 14])]
-    depth, dt, nt, stride = 4, 0.005, 3, 40
+    depth, dt, nt, stride = 4, 0.005, 3, 120
     mu = inputs.Optical(lin=(1.0, 1.0))
     with chfpe.Batch([model, model], grids, depth=depth, dt=dt, precision=32, bf16_tier=3,
                      max_batch=3) as b:

@@ -450,3 +450,25 @@ def test_sample_device_matches_oracle(mode, monkeypatch):
         assert launches < 20
     np.testing.assert_allclose(got[:, :ns], want, rtol=1e-11, atol=1e-13 * np.abs(want).max())
     assert np.all(got[:, ns:] == 0)                         # ld > nsamples: the gap untouched
+
+
+@pytest.mark.parametrize("d,n,depth,dt,stride,n2,nt,mb", [
+    (1, [37, 44], 4, 0.005, 20, 30, 5, 2),            # chunks 2 + 2 + 1; scalar stage kernel
+    (2, [12, 11, 12, 12], 3, 0.01, 25, 40, 4, 4),     # vectorised stage kernel
+])
+def test_response3_matches_oracle(d, n, depth, dt, stride, n2, nt, mb):
+    """Eq. 3Dresponse at one waiting time: both precisions against the oracle (which propagates
+    every t1 branch on its own): FP64 1e-10, FP32 1e-4 of max|R3|."""
+    chfpe = _chfpe()
+    model = _model(d)
+    grid = inputs.default_grid(model, n, cut=12.0, nsigma=5.0)
+    pb = oracle.Problem(model, grid, depth)
+    Weq = _rounded(ref.hierarchy_state(ref.boltzmann_sym(model, grid), pb.M), 32)
+    mu = inputs.Optical(lin=(1.0, 0.6, 0.3), quad=[[0.3, 0.1, 0.0], [0.1, -0.2, 0.0], [0, 0, 0.1]])
+    Pi = inputs.Optical(lin=(0.5, 1.0, 0.2), quad=[[0.8, 0.0, 0.1], [0.0, 0.4, 0.0], [0.1, 0, 0.2]])
+    want = oracle.response3(pb, mu, Pi, Pi, mu, Weq, dt, nt, n2, nt, stride)
+    for prec, tol in ((64, 1e-10), (32, 1e-4)):
+        with chfpe.Handle(model, grid, depth=depth, dt=dt, precision=prec, max_batch=mb) as h:
+            h.set_equilibrium(Weq)
+            got = h.response3(mu, Pi, Pi, mu, nt, n2, nt, stride)
+        assert _norm_err(got, want) < tol, (prec, _norm_err(got, want))

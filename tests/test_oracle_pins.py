@@ -257,6 +257,50 @@ def test_moment_closure_one_mode_deep_hierarchy():
         np.testing.assert_allclose(R, want, rtol=0, atol=1e-6 * np.abs(want).max())
 
 
+def test_r3_moment_closure_one_mode_deep_hierarchy():
+    """Eq. 3Dresponse against the exact moment closure: one harmonic mode with a Drude bath at
+    depth 4, linear and quadratic optics in several orders, waiting time 0.15."""
+    m, w, kT = 0.9, 1.1, 1.2
+    model = inputs.Model(nmodes=1, kT=kT, m=(m,), omega=(w,), zeta=(0.6,), gamma=(1.3,),
+                         V_LL=(0.9,))
+    depth = 4
+    mc = ref.MomentClosure(model, depth, K=2)
+    mu = inputs.Optical(lin=(1.0,), quad=[[0.4]])
+    Pi = inputs.Optical(lin=(0.5,), quad=[[1.1]])
+    dt, nt, stride, n2 = 0.01, 5, 20, 15
+    grid = _scaled_grid1(m, w, kT, 128)
+    pb = oracle.Problem(model, grid, depth)
+    Weq = ref.hierarchy_state(ref.boltzmann_sym(model, grid), pb.M)
+    W0 = ref.boltzmann_grid(model, grid)
+    for ops in [(mu, Pi, Pi, mu), (Pi, mu, mu, Pi), (mu, mu, Pi, Pi), (Pi, Pi, Pi, Pi)]:
+        R = oracle.response3(pb, *ops, Weq, dt, nt, n2, nt, stride)
+        want = mc.response3(*ops, W0, grid, dt, nt, n2, nt, stride)
+        assert np.abs(want).max() > 1e-3
+        np.testing.assert_allclose(R, want, rtol=0, atol=1e-6 * np.abs(want).max())
+
+
+def test_r3_all_linear_vanishes():
+    """Harmonic mode, linear A, B, C, D: the third-order response is zero (each linear insertion
+    lowers the polynomial degree of the adjoint observable by one)."""
+    model = inputs.Model(nmodes=1, kT=BO["kT"], m=(BO["m"],), omega=(BO["w"],),
+                         zeta=(BO["zeta"],), gamma=(BO["gamma"],), V_LL=(BO["V"],))
+    mu = inputs.Optical(lin=(1.0,))
+    Pi = inputs.Optical(lin=(0.6,), quad=[[1.5]])
+    dt, nt, stride, n2 = 0.01, 4, 25, 10
+
+    def run(ops):
+        def f(n):
+            grid = _scaled_grid1(BO["m"], BO["w"], BO["kT"], n)
+            pb = oracle.Problem(model, grid, 3)
+            Weq = ref.hierarchy_state(ref.boltzmann_sym(model, grid), pb.M)
+            return oracle.response3(pb, *ops, Weq, dt, nt, n2, nt, stride)
+        return f
+
+    scale = np.abs(run((mu, Pi, Pi, mu))(64)).max()
+    # sixth-order convergence to zero (2.5e-6 of the quadratic-optics R3 at 128 points)
+    _converges(run((mu, mu, mu, mu)), np.zeros((nt, nt)), 1e-5, scale=scale)
+
+
 @pytest.mark.slow
 def test_moment_closure_two_coupled_modes():
     # 4D grids are coarse (h ~ 0.5 sigma at 28 points), so the O(h^6) error of the stencil is
