@@ -354,14 +354,15 @@ chfpe_status chfpe_surrogate_gemm(const void *A, int ta, int lda, const void *B,
  * 6 and 7 as 3 with 256 and 64 threads per block; 8 as 3 with L1 prefetch hints for the next
  * member's q-neighbours; 9 as 3 with the next member's q-neighbours copied asynchronously into
  * per-thread shared-memory slots; 10 and 11 as 3 with register budgets for 3 and 2 blocks per
- * SM; 12-14 as 3 with a tiled block-to-row mapping (each block covers a small box of grid rows
- * along (q_{d-1}, q_d, p_{d-1}): 2 x 2 x 4, 1 x 4 x 4, 4 x 4 x 1 rows) so that stencil
- * neighbours along those axes are mostly loaded by the same block; 15 as 12 with 256 threads
- * (2 x 4 x 4 box); 16 as 3 and 17 as 12 with each member's result stored as soon as its last
- * contribution is in.  Shapes 3-17 need the last p extent to be a multiple of 4, and the tiled
- * shapes (12-15, 17) need a quarter of it to divide the block's thread count; a shape that does
- * not apply runs shape 0 (and is not timed).
- * All shapes compute the same arithmetic in the same order.  Shape 4's waits are bounded; a wait
+ * SM; 12-17 store each member as soon as its last contribution is in ("early stores"), 13-16
+ * processing the members in storage order (13 four points per thread with registers for 5
+ * blocks per SM, 14 two points for 8 blocks, 15 four points with 256 threads, 16 four points for
+ * 4 blocks), 12 and 17 in an order that keeps fewer right-hand sides open (registers for 5 and 4
+ * blocks per SM).  Shapes 3-17 need the last p extent to be a multiple of 4 and fall back to
+ * shape 0 otherwise.
+ * All shapes compute the same arithmetic; 12 and 17 sum each member's contributions in their
+ * processing order, the others in storage order (equal up to rounding).  Shape 4's waits are
+ * bounded; a wait
  * that gives up makes the next synchronising call return CHFPE_ETIMEOUT.
  */
 #define CHFPE_STAGE_VARIANTS 18

@@ -26,6 +26,9 @@ Parity status per function (what pins it; the pins live in ``tests/test_oracle_p
   response1/2  closed forms and moment closure above
   response3    the moment closure (one mode, deep hierarchy, linear and quadratic optics) and
                the vanishing third-order response of the harmonic / all-linear case
+  h_*          (Hermite-function momenta, Appendix A) the antisymmetry of the ladder generator,
+               Boltzmann stationarity, the Brownian closed form, the moment closure, and the
+               grid representation's responses on the same model
 """
 from __future__ import annotations
 
@@ -109,6 +112,12 @@ def _load():
                                           ctypes.c_long, _DP]
             lib.orc_response2.argtypes = [P, O, O, O, _DP, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_long, _DP]
+            lib.orc_h_rhs.argtypes = [P, _DP, _DP]
+            lib.orc_h_rk4.argtypes = [P, _DP, ctypes.c_double, ctypes.c_long]
+            lib.orc_h_insert.argtypes = [P, O, _DP, _DP]
+            lib.orc_h_observe.argtypes = [P, O, _DP]
+            lib.orc_h_observe.restype = ctypes.c_double
+            lib.orc_h_boltzmann.argtypes = [P, _DP]
             _lib = lib
     return _lib
 
@@ -319,4 +328,72 @@ def response3(pb: Problem, A, B, C, D, Weq, dt: float, nt1: int, n2: int, nt3: i
                 X = rk4(pb, X, dt, stride)
         if a + 1 < nt1:
             W = rk4(pb, W, dt, stride)
+    return R
+
+
+# ------------------------------------------------------------------------------------------
+# Hermite-function representation of the momenta (Sec. III A, Appendix A, Eq. HEOM2FP-H):
+# states [member][q_1..q_d][k_1..k_d]; the grid's np[s] is the number K_s of Hermite functions
+# ------------------------------------------------------------------------------------------
+
+def h_rhs(pb: Problem, C) -> np.ndarray:
+    C = _as_state(pb, C)
+    out = np.empty_like(C)
+    if _load().orc_h_rhs(pb._ptr(), _p(C), _p(out)):
+        raise RuntimeError("orc_h_rhs failed")
+    return out
+
+
+def h_rk4(pb: Problem, C, dt: float, nsteps: int) -> np.ndarray:
+    y = _as_state(pb, C).copy()
+    if _load().orc_h_rk4(pb._ptr(), _p(y), float(dt), int(nsteps)):
+        raise RuntimeError("orc_h_rk4 failed")
+    return y
+
+
+def h_insert(pb: Problem, X, C) -> np.ndarray:
+    C = _as_state(pb, C)
+    out = np.empty_like(C)
+    x = _optical(X)
+    if _load().orc_h_insert(pb._ptr(), ctypes.byref(x), _p(C), _p(out)):
+        raise RuntimeError("orc_h_insert failed")
+    return out
+
+
+def h_observe(pb: Problem, Cop, C) -> float:
+    C = _as_state(pb, C)
+    x = _optical(Cop)
+    return float(_load().orc_h_observe(pb._ptr(), ctypes.byref(x), _p(C)))
+
+
+def h_boltzmann(pb: Problem) -> np.ndarray:
+    out = pb.zeros()
+    if _load().orc_h_boltzmann(pb._ptr(), _p(out)):
+        raise RuntimeError("orc_h_boltzmann failed")
+    return out
+
+
+def h_response1(pb: Problem, A, C, Ceq, dt: float, nt: int, stride: int) -> np.ndarray:
+    """Eq. 1Dresponse in the Hermite representation: insert, then observe every stride steps."""
+    X = h_insert(pb, A, Ceq)
+    R = np.zeros(nt)
+    for k in range(nt):
+        R[k] = h_observe(pb, C, X)
+        if k + 1 < nt:
+            X = h_rk4(pb, X, dt, stride)
+    return R
+
+
+def h_response2(pb: Problem, A, B, C, Ceq, dt: float, nt1: int, nt2: int, stride: int) -> np.ndarray:
+    """Eq. 2Dresponse in the Hermite representation, each t1 branch propagated on its own."""
+    W = h_insert(pb, A, Ceq)
+    R = np.zeros((nt1, nt2))
+    for i in range(nt1):
+        X = h_insert(pb, B, W)
+        for j in range(nt2):
+            R[i, j] = h_observe(pb, C, X)
+            if j + 1 < nt2:
+                X = h_rk4(pb, X, dt, stride)
+        if i + 1 < nt1:
+            W = h_rk4(pb, W, dt, stride)
     return R

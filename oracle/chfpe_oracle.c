@@ -580,3 +580,226 @@ int orc_response2(const orc_problem *pr, const orc_optical *A, const orc_optical
     free(Wc); free(Wb);
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Hermite-function representation of the momenta (Sec. III A, Appendix A, Eq. HEOM2FP-H)    */
+/* ------------------------------------------------------------------------------------------ */
+/*
+ * The paper expands every member as W^(n) = psi_0(p) exp(-U/2kT) sum_k c^(n)_k(q) psi_k(p) with
+ * the Hermite functions psi_j(p) = H_j(p/a) exp(-p^2/2a^2) / sqrt(2^j j! a sqrt(pi)),
+ * a = sqrt(2 m kT) (one index k_s per mode).  psi_0(p) exp(-U/2kT) is exp(-H/2kT) up to a
+ * constant, so the coefficients are those of the symmetrised member g^(n) in the orthonormal
+ * functions psi_k:  g^(n)(q,p) = sum_k c^(n)_k(q) prod_s psi_{k_s}(p_s)  (with the member scale
+ * lambda_n of the grid representation).  The ladder identities
+ *     p psi_k   = sqrt(m kT) [sqrt(k) psi_{k-1} + sqrt(k+1) psi_{k+1}]
+ *     d/dp psi_k = [sqrt(k) psi_{k-1} - sqrt(k+1) psi_{k+1}] / (2 sqrt(m kT))
+ * turn the symmetrised hierarchy into (coefficient of psi_k, member n, mode s terms summed)
+ *     dc^(n)_k/dt = sum_s [ sqrt(k_s+1) D+_s c^(n)_{k+e_s} - sqrt(k_s) D-_s c^(n)_{k-e_s} ]
+ *                 - sum_s n_s gamma_s c^(n)_k
+ *                 - sum_s sqrt((n_s+1) c_s) V_s' sqrt(k_s) / sqrt(m_s kT) c^(n+e_s)_{k-e_s}
+ *                 + sum_s sqrt(n_s c_s) V_s' sqrt(k_s+1) / sqrt(m_s kT) c^(n-e_s)_{k+e_s}
+ *     D+-_s = dU/dq_s / (2 sqrt(m_s kT)) -+ (sqrt(m_s kT) / m_s) d/dq_s,
+ * which is Eq. HEOM2FP-H (its Theta^(s)_j and Phi^(s)_j with the member scale lambda_n divided
+ * out); (d/dp - p/2mkT) psi_k = -sqrt(k+1) psi_{k+1} / sqrt(mkT) is the raising operator the
+ * Phi link and the insertion use, (d/dp + p/2mkT) the matching lowering operator.  Coefficients
+ * with k_s outside [0, K_s) are zero (truncation).  d/dq_s is the same 6th-order central
+ * difference with zero values outside the q-grid.
+ *
+ * Layout: [member][q_1]..[q_d][k_1]..[k_d], k_d fastest; the orc_problem's np[s] holds K_s
+ * (pmin/pmax are not used).
+ */
+
+#define ORC_PI 3.14159265358979323846
+
+static int hgeom_init(const orc_problem *pr, orc_geom *g)
+{
+    int r = geom_init(pr, g);
+    if (r) return r;
+    for (int s = 0; s < g->d; ++s) {   /* the k axes are indices, not coordinates */
+        g->lo[g->d + s] = 0.0;
+        g->h[g->d + s] = 1.0;
+    }
+    return 0;
+}
+
+/* coefficient c^(member)_k at the point x shifted by `dk` along k_s; 0 outside [0, K_s) */
+static double hcoef(const orc_geom *g, const double *C, int member, long x, const long *idx, int s,
+                    int dk)
+{
+    if (member < 0) return 0.0;
+    long k = idx[g->d + s] + dk;
+    if (k < 0 || k >= g->n[g->d + s]) return 0.0;
+    return C[(long)member * g->P + x + dk * g->stride[g->d + s]];
+}
+
+/* d/dq_s of c^(i)_{k + dk e_s} at the point x (zero outside the q-grid and outside [0, K_s)) */
+static double hderiv_q(const orc_geom *g, const double *C, int i, long x, const long *idx, int s,
+                       int dk)
+{
+    long k = idx[g->d + s] + dk;
+    if (k < 0 || k >= g->n[g->d + s]) return 0.0;
+    return deriv_axis(g, C + (long)i * g->P, x + dk * g->stride[g->d + s], idx, s);
+}
+
+int orc_h_rhs(const orc_problem *pr, const double *Cin, double *K)
+{
+    orc_geom g;
+    if (hgeom_init(pr, &g)) return -1;
+    const int d = g.d;
+    const long P = g.P;
+    const double kT = pr->kT;
+    int up[ORC_MAXM][ORC_MAXD], dn[ORC_MAXM][ORC_MAXD];
+    for (int i = 0; i < g.M; ++i)
+        for (int s = 0; s < d; ++s) {
+            int n[ORC_MAXD] = {0, 0, 0};
+            for (int r = 0; r < d; ++r) n[r] = g.mem[i][r];
+            n[s] += 1;
+            up[i][s] = member_index(&g, n);
+            n[s] -= 2;
+            dn[i][s] = (n[s] >= 0) ? member_index(&g, n) : -1;
+        }
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int i = 0; i < g.M; ++i) {
+        for (long x = 0; x < P; ++x) {
+            long idx[2 * ORC_MAXD];
+            double q[ORC_MAXD];
+            decode(&g, x, idx);
+            for (int s = 0; s < d; ++s) q[s] = g.lo[s] + idx[s] * g.h[s];
+            double val = 0.0;
+            for (int s = 0; s < d; ++s) {
+                const double smkT = sqrt(pr->m[s] * kT);
+                const double F = orc_dUdq(pr, q, s);
+                const double ks = (double)idx[d + s];
+                /* sqrt(k+1) D+ c_{k+e_s} - sqrt(k) D- c_{k-e_s} */
+                const double cp = hcoef(&g, Cin, i, x, idx, s, +1);
+                const double cm = hcoef(&g, Cin, i, x, idx, s, -1);
+                const double dcp = hderiv_q(&g, Cin, i, x, idx, s, +1);
+                const double dcm = hderiv_q(&g, Cin, i, x, idx, s, -1);
+                val += sqrt(ks + 1.0) * (F / (2.0 * smkT) * cp - smkT / pr->m[s] * dcp);
+                val -= sqrt(ks) * (F / (2.0 * smkT) * cm + smkT / pr->m[s] * dcm);
+                /* hierarchy links */
+                const double c = pr->zeta[s] * pr->gamma[s] * pr->m[s] * kT;
+                const double Vp = dVdq(pr, s, q[s]);
+                const double ni = (double)g.mem[i][s];
+                val -= sqrt((ni + 1.0) * c) * Vp * sqrt(ks) / smkT *
+                       hcoef(&g, Cin, up[i][s], x, idx, s, -1);
+                val += sqrt(ni * c) * Vp * sqrt(ks + 1.0) / smkT *
+                       hcoef(&g, Cin, dn[i][s], x, idx, s, +1);
+            }
+            double damp = 0.0;
+            for (int s = 0; s < d; ++s) damp += g.mem[i][s] * pr->gamma[s];
+            val -= damp * Cin[(long)i * P + x];
+            K[(long)i * P + x] = val;
+        }
+    }
+    return 0;
+}
+
+int orc_h_rk4(const orc_problem *pr, double *y, double dt, long nsteps)
+{
+    orc_geom g;
+    if (hgeom_init(pr, &g)) return -1;
+    const long N = (long)g.M * g.P;
+    double *k1 = malloc(sizeof(double) * N), *k2 = malloc(sizeof(double) * N);
+    double *k3 = malloc(sizeof(double) * N), *k4 = malloc(sizeof(double) * N);
+    double *tmp = malloc(sizeof(double) * N);
+    if (!k1 || !k2 || !k3 || !k4 || !tmp) {
+        free(k1); free(k2); free(k3); free(k4); free(tmp);
+        return -3;
+    }
+    for (long step = 0; step < nsteps; ++step) {
+        orc_h_rhs(pr, y, k1);
+#pragma omp parallel for schedule(static)
+        for (long j = 0; j < N; ++j) tmp[j] = y[j] + 0.5 * dt * k1[j];
+        orc_h_rhs(pr, tmp, k2);
+#pragma omp parallel for schedule(static)
+        for (long j = 0; j < N; ++j) tmp[j] = y[j] + 0.5 * dt * k2[j];
+        orc_h_rhs(pr, tmp, k3);
+#pragma omp parallel for schedule(static)
+        for (long j = 0; j < N; ++j) tmp[j] = y[j] + dt * k3[j];
+        orc_h_rhs(pr, tmp, k4);
+#pragma omp parallel for schedule(static)
+        for (long j = 0; j < N; ++j) y[j] += dt / 6.0 * (k1[j] + 2.0 * k2[j] + 2.0 * k3[j] + k4[j]);
+    }
+    free(k1); free(k2); free(k3); free(k4); free(tmp);
+    return 0;
+}
+
+/* X^x on every member (Eq. Opticalexc): sum_s dX/dq_s (d/dp_s - p_s/2m_skT) acts on psi_k as
+ * -sqrt(k_s+1)/sqrt(m_s kT) psi_{k+e_s}:  out_k = -sum_s dX/dq_s sqrt(k_s)/sqrt(m_s kT) c_{k-e_s} */
+int orc_h_insert(const orc_problem *pr, const orc_optical *X, const double *Cin, double *out)
+{
+    orc_geom g;
+    if (hgeom_init(pr, &g)) return -1;
+    const int d = g.d;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int i = 0; i < g.M; ++i) {
+        for (long x = 0; x < g.P; ++x) {
+            long idx[2 * ORC_MAXD];
+            double q[ORC_MAXD];
+            decode(&g, x, idx);
+            for (int s = 0; s < d; ++s) q[s] = g.lo[s] + idx[s] * g.h[s];
+            double v = 0.0;
+            for (int s = 0; s < d; ++s)
+                v -= orc_optical_grad(X, d, q, s) * sqrt((double)idx[d + s]) /
+                     sqrt(pr->m[s] * pr->kT) * hcoef(&g, Cin, i, x, idx, s, -1);
+            out[(long)i * g.P + x] = v;
+        }
+    }
+    return 0;
+}
+
+/* integral C(q) exp(-H/2kT) g^(0) dq dp: the p-integral of exp(-p^2/4mkT) psi_k is
+ * sqrt(a sqrt(pi)) for k = 0 and 0 otherwise, so only c^(0)_0 contributes; rectangle rule on
+ * the q nodes */
+double orc_h_observe(const orc_problem *pr, const orc_optical *C, const double *Cin)
+{
+    orc_geom g;
+    if (hgeom_init(pr, &g)) return NAN;
+    const int d = g.d;
+    double pre = 1.0;
+    for (int s = 0; s < d; ++s) pre *= g.h[s] * sqrt(sqrt(2.0 * pr->m[s] * pr->kT) * sqrt(ORC_PI));
+    const long Pq = g.P / g.stride[d - 1];   /* q points: P = Pq * prod K_s */
+    double sum = 0.0;
+    for (long x = 0; x < g.P; x += g.stride[d - 1]) {
+        long idx[2 * ORC_MAXD];
+        double q[ORC_MAXD];
+        decode(&g, x, idx);
+        for (int s = 0; s < d; ++s) q[s] = g.lo[s] + idx[s] * g.h[s];
+        sum += orc_optical_value(C, d, q) * exp(-orc_potential(pr, q) / (2.0 * pr->kT)) * Cin[x];
+    }
+    (void)Pq;
+    return pre * sum;
+}
+
+/* equilibrium sample: c^(0)_0(q) = exp(-U/2kT) prod_s sqrt(a_s sqrt(pi)) / Z with
+ * Z = (h^d sum_q exp(-U/kT)) prod_s sqrt(2 pi m_s kT) (the p-integral taken exactly), so that
+ * the density integrates to 1; every other coefficient and member is 0 */
+int orc_h_boltzmann(const orc_problem *pr, double *Cout)
+{
+    orc_geom g;
+    if (hgeom_init(pr, &g)) return -1;
+    const int d = g.d;
+    memset(Cout, 0, sizeof(double) * (long)g.M * g.P);
+    double Zq = 0.0, norm = 1.0, vol = 1.0;
+    for (int s = 0; s < d; ++s) {
+        vol *= g.h[s];
+        norm *= sqrt(sqrt(2.0 * pr->m[s] * pr->kT) * sqrt(ORC_PI)) / sqrt(2.0 * ORC_PI * pr->m[s] * pr->kT);
+    }
+    for (long x = 0; x < g.P; x += g.stride[d - 1]) {
+        long idx[2 * ORC_MAXD];
+        double q[ORC_MAXD];
+        decode(&g, x, idx);
+        for (int s = 0; s < d; ++s) q[s] = g.lo[s] + idx[s] * g.h[s];
+        Zq += exp(-orc_potential(pr, q) / pr->kT);
+    }
+    Zq *= vol;
+    for (long x = 0; x < g.P; x += g.stride[d - 1]) {
+        long idx[2 * ORC_MAXD];
+        double q[ORC_MAXD];
+        decode(&g, x, idx);
+        for (int s = 0; s < d; ++s) q[s] = g.lo[s] + idx[s] * g.h[s];
+        Cout[x] = exp(-orc_potential(pr, q) / (2.0 * pr->kT)) * norm / Zq;
+    }
+    return 0;
+}

@@ -754,8 +754,6 @@ static chfpe_status autotune(chfpe_handle *h) {
         for (int v = 0; v < CHFPE_STAGE_VARIANTS && e == cudaSuccess; ++v) {
             if (v >= 3 && npd % 4 != 0) continue;
             if ((v == 4 || v == 5) && h->d != 2) continue;
-            RowTile rt;
-            if (tiled_variant(v) && !row_tile(v, h->d, h->n, &rt)) continue;
             if (round > 0 && h->tune_us[v] < 0) continue;   // disqualified in an earlier round
             h->variant = v;
             launch_stage<float>(h, a, batch);   // warm-up

@@ -27,6 +27,8 @@
 #include <stdint.h>
 #include <cuda_bf16.h>
 
+#include <utility>
+
 namespace chfpe {
 
 constexpr int kMaxD = 3;
@@ -52,9 +54,10 @@ struct MemberTable {
     int n[M][3];
     int up[M][3];   // index of n + e_s, or -1
     int dn[M][3];   // index of n - e_s, or -1
-    int last[M];    // the last member (in processing order) that adds to member i's right-hand
-                    // side: i itself or its highest up-neighbour
-    constexpr MemberTable() : n{}, up{}, dn{}, last{} {
+    int order[M];   // a processing order with few right-hand sides open at once (see below)
+    int last[M];    // the step of that order after which member i's right-hand side is complete
+    int last_st[M]; // the same in storage order: i itself or its highest up-neighbour
+    constexpr MemberTable() : n{}, up{}, dn{}, order{}, last{}, last_st{} {
         int c = 0;
         for (int t = 0; t <= DEPTH; ++t) {
             if (D == 1) {
@@ -85,13 +88,81 @@ struct MemberTable {
                     if (isdn) dn[i][s] = j;
                 }
             }
+        // Processing order: member m adds to the accumulators of m and of its neighbours m +- e_s,
+        // so accumulator i is open from the first to the last of those members' steps.  A greedy
+        // order (each step takes the member that leaves the fewest accumulators open, from the best
+        // of all starting members) keeps 7 of the 15 two-mode depth-4 accumulators open at most,
+        // against 10 in storage (tier) order.  The contribution relation is symmetric; nb[i] lists
+        // member i and its neighbours.
+        int nb[M][7] = {}, deg[M] = {};
         for (int i = 0; i < M; ++i) {
-            last[i] = i;
+            last_st[i] = i;
             for (int s = 0; s < 3; ++s)
-                if (up[i][s] > last[i]) last[i] = up[i][s];
+                if (up[i][s] > last_st[i]) last_st[i] = up[i][s];
+            nb[i][deg[i]++] = i;
+            for (int s = 0; s < 3; ++s) {
+                if (up[i][s] >= 0) nb[i][deg[i]++] = up[i][s];
+                if (dn[i][s] >= 0) nb[i][deg[i]++] = dn[i][s];
+            }
+        }
+        int best_live = M + 1;
+        for (int start = 0; start < M; ++start) {
+            int ord[M] = {}, cnt[M] = {};
+            bool done[M] = {};
+            for (int t = 0; t < M; ++t) {
+                int pick = -1, pick_delta = M + 1;
+                for (int m = 0; m < M; ++m) {
+                    if (done[m] || (t == 0 && m != start)) continue;
+                    // change in open accumulators when m is processed next
+                    int delta = 0;
+                    for (int k = 0; k < deg[m]; ++k) {
+                        const int i = nb[m][k];
+                        const bool was = cnt[i] > 0 && cnt[i] < deg[i];
+                        const bool now = cnt[i] + 1 < deg[i];
+                        delta += (now ? 1 : 0) - (was ? 1 : 0);
+                    }
+                    if (delta < pick_delta) { pick_delta = delta; pick = m; }
+                }
+                done[pick] = true;
+                ord[t] = pick;
+                for (int k = 0; k < deg[pick]; ++k) ++cnt[nb[pick][k]];
+            }
+            // the most accumulators live during one step (touched, not yet stored)
+            int pos[M] = {}, first[M] = {}, lastt[M] = {};
+            for (int t = 0; t < M; ++t) pos[ord[t]] = t;
+            for (int i = 0; i < M; ++i) {
+                first[i] = M;
+                lastt[i] = -1;
+                for (int k = 0; k < deg[i]; ++k) {
+                    const int u = pos[nb[i][k]];
+                    if (u < first[i]) first[i] = u;
+                    if (u > lastt[i]) lastt[i] = u;
+                }
+            }
+            int live = 0;
+            for (int t = 0; t < M; ++t) {
+                int l = 0;
+                for (int i = 0; i < M; ++i) l += (first[i] <= t && lastt[i] >= t) ? 1 : 0;
+                if (l > live) live = l;
+            }
+            if (live < best_live) {
+                best_live = live;
+                for (int t = 0; t < M; ++t) order[t] = ord[t];
+                for (int i = 0; i < M; ++i) last[i] = lastt[i];
+            }
         }
     }
 };
+
+template <int D, int DEPTH>
+constexpr MemberTable<D, DEPTH> kMemberTable{};
+
+// f(std::integral_constant<int, S>()) for S = 0, 1, ...: a loop whose index is a compile-time
+// constant in the body (member indices, and through them accumulator indices, stay static)
+template <typename F, int... S>
+__device__ __forceinline__ void static_steps(F &&f, std::integer_sequence<int, S...>) {
+    (f(std::integral_constant<int, S>()), ...);
+}
 
 // ------------------------------------------------------------------------------------------
 // per-instance geometry and coefficients; stage arguments
@@ -344,11 +415,13 @@ __device__ __forceinline__ void prefetch_member(const S *g, const Geo<T> &a, int
 // vectors of member m + 1 into its own shared-memory slots by cp.async while member m is
 // computed (two slot sets, 6 D float4 each; the thread reads only what it copied itself, so
 // cp.async.wait_group orders everything and no block barrier is needed)
-// ES = true (early stores): member i's result is written as soon as the last member adding to it
-// (MemberTable::last) has been processed, instead of after the whole hierarchy -- the same values,
-// with fewer accumulators live at once.
+// ES > 0 (early stores): member i's result is written as soon as the last member adding to it has
+// been processed, instead of after the whole hierarchy -- fewer accumulators live at once.  ES = 1
+// processes the members in storage order (10 of 15 accumulators open at most for two modes at
+// depth 4); ES = 2 in MemberTable::order (7 of 15), which sums the contributions to one member in
+// another order than the other shapes (equal up to rounding).
 template <typename T, int D, int DEPTH, int V, int M32, bool NC = true, bool PF = false, int QS = 0,
-          bool ES = false>
+          int ES = 0>
 __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, const char *y,
                                              char *out, T c, int x0) {
     constexpr MemberTable<D, DEPTH> tab{};
@@ -426,8 +499,9 @@ __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, co
     };
     if constexpr (QS > 0) q_issue(0, 0);
 
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
+    auto member_step = [&](auto stepc) {
+        constexpr int step = decltype(stepc)::value;
+        constexpr int m = ES == 2 ? kMemberTable<D, DEPTH>.order[step] : step;
         if constexpr (QS > 0) {
             if (m + 1 < M) {
                 q_issue(m + 1, (m + 1) & 1);
@@ -468,63 +542,27 @@ __device__ __forceinline__ void stage_points(const Geo<T> &a, const char *in, co
                 }
             }
         }
-        if constexpr (ES) {
+        if constexpr (ES > 0) {
 #pragma unroll
             for (int i = 0; i < M; ++i)
-                if (tab.last[i] == m) store_member(i);
+                if ((ES == 2 ? tab.last[i] : tab.last_st[i]) == step) store_member(i);
         }
-    }
+    };
+    static_steps(member_step, std::make_integer_sequence<int, M>());
 
-    if constexpr (!ES) {
+    if constexpr (ES == 0) {
 #pragma unroll
         for (int m = 0; m < M; ++m) store_member(m);
     }
 }
 
 template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32, bool PF = false,
-          bool QST = false, bool ES = false>
+          bool QST = false, int ES = 0>
 __global__ void __launch_bounds__(NT, MINB) stage_vec_kernel(const StageArgs<T> a) {
     const int x0 = (blockIdx.x * NT + threadIdx.x) * V;
     if (x0 >= a.g.P) return;
     const long long boff = (long long)blockIdx.y * a.state_bytes;
     stage_points<T, D, DEPTH, V, M32, true, PF, QST ? NT : 0, ES>(
-        a.g, a.in + boff, a.y ? a.y + boff : nullptr, a.out + boff, a.c, x0);
-}
-
-// ------------------------------------------------------------------------------------------
-// the same stage with a tiled block -> row mapping.  A "row" is one line of the fastest axis
-// p_d (every axis but p_d fixed); tpr = n_pd / V threads cover a row.  Each block covers a box of
-// B[0] x .. x B[2d-2] rows (B = 1 on axes not tiled), so that the stencil taps of one thread
-// along a tiled axis are, for the interior of the box, points another thread of the block
-// loads too (L1 hits instead of L2 round trips).  Boxes are numbered with the last row axis
-// fastest; a box that sticks out of the grid leaves its outside threads idle.
-// ------------------------------------------------------------------------------------------
-
-struct RowTile {
-    int B[5];       // box extent per row axis (q_1..q_d, p_1..p_{d-1})
-    int nb[5];      // boxes per row axis: ceil(n / B)
-    int tpr;        // threads per row (n_pd / V)
-    int rows;       // rows per box (product of B)
-};
-
-template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32, bool ES = false>
-__global__ void __launch_bounds__(NT, MINB) stage_tile_kernel(const StageArgs<T> a, const RowTile t) {
-    constexpr int NR = 2 * D - 1;
-    int lr = threadIdx.x / t.tpr;              // row inside the box
-    if (lr >= t.rows) return;
-    const int lane = threadIdx.x - lr * t.tpr;
-    int b = blockIdx.x;
-    int x0 = lane * V;
-#pragma unroll
-    for (int ax = NR - 1; ax >= 0; --ax) {
-        const int c = (b % t.nb[ax]) * t.B[ax] + lr % t.B[ax];
-        b /= t.nb[ax];
-        lr /= t.B[ax];
-        if (c >= a.g.n[ax]) return;
-        x0 += c * a.g.st[ax];
-    }
-    const long long boff = (long long)blockIdx.y * a.state_bytes;
-    stage_points<T, D, DEPTH, V, M32, true, false, 0, ES>(
         a.g, a.in + boff, a.y ? a.y + boff : nullptr, a.out + boff, a.c, x0);
 }
 

@@ -33,16 +33,16 @@ constexpr int kVec = 2;
 //      memory slots (no block barrier)
 //  10  shape 3 with registers for 3 blocks per SM (168)
 //  11  shape 3 with registers for 2 blocks per SM (255)
-//  12  shape 3 with a tiled block -> row mapping (stage_tile_kernel): box of 2 x 2 x 4 rows
-//      along (q_{d-1}, q_d, p_{d-1}) for 16-row blocks
-//  13  as 12 with a 1 x 4 x 4 box
-//  14  as 12 with a 4 x 4 x 1 box
-//  15  as 12 with 256 threads, 2 x 4 x 4 box (2 blocks per SM)
-//  16  shape 3 with early stores (each member written once its last contribution is in)
-//  17  shape 12 with early stores
-// Shapes 3-17 need n_pd % 4 == 0; the tiled shapes 12-15 and 17 also need n_pd / 4 to divide
-// the block's thread count (a power of two up to 128).  A shape that does not apply runs
-// shape 0.
+//  12  early stores (ES: each member stored once its last contribution is in) in an order that
+//      keeps few accumulators open (MemberTable::order), 4 points, 128 threads, 5 blocks per SM
+//  13  ES in storage order, 4 points, 128 threads, 5 blocks per SM (102 registers)
+//  14  ES in storage order, 2 points, 128 threads, 8 blocks per SM (64)
+//  15  ES in storage order, 4 points, 256 threads, 2 blocks per SM
+//  16  ES in storage order, 4 points, 128 threads, 4 blocks per SM (128)
+//  17  ES in the open-accumulator order, 4 points, 128 threads, 4 blocks per SM
+// Shapes 3-17 need n_pd % 4 == 0 (shape 0 runs otherwise).  (Shapes with a block
+// covering a small box of grid rows along (q_{d-1}, q_d, p_{d-1}), meant to turn q-neighbour taps
+// into L1 hits, ran 2-20 % slower than shape 3 on the two-mode workload and were removed.)
 constexpr int kStageVariants = 18;
 
 constexpr bool tunable(int T_size, int D, int DEPTH) {
@@ -50,49 +50,8 @@ constexpr bool tunable(int T_size, int D, int DEPTH) {
                            (D == 3 && DEPTH == 2));
 }
 
-constexpr bool tiled_variant(int v) { return (v >= 12 && v <= 15) || v == 17; }
-
-// the box of a tiled shape for a grid whose p_d axis has npd points: rows per block
-// R = NT / (npd / 4), spread over (p_{d-1}, q_d, q_{d-1}) up to the shape's target extents, the
-// rest on p_{d-1}; false when the shape does not apply
-inline bool row_tile(int variant, int d, const int *n, RowTile *t) {
-    if (!tiled_variant(variant)) return false;
-    const int npd = n[2 * d - 1];
-    const int NT = variant == 15 ? 256 : 128;
-    if (npd % 4 != 0) return false;
-    const int tpr = npd / 4;
-    if (tpr > NT || NT % tpr != 0) return false;
-    int R = NT / tpr;
-    int target[3];   // p_{d-1}, q_d, q_{d-1}
-    switch (variant) {
-    case 13: target[0] = 4; target[1] = 4; target[2] = 1; break;
-    case 14: target[0] = 1; target[1] = 4; target[2] = 4; break;
-    case 15: target[0] = 4; target[1] = 4; target[2] = 2; break;
-    default: target[0] = 4; target[1] = 2; target[2] = 2; break;
-    }
-    const int NR = 2 * d - 1;
-    for (int ax = 0; ax < 5; ++ax) t->B[ax] = 1;
-    int axes[3] = {NR - 1, d - 1, d - 2};          // p_{d-1}, q_d, q_{d-1}
-    if (d == 1) { axes[0] = 0; axes[1] = -1; axes[2] = -1; }
-    for (int k = 0; k < 3 && R > 1; ++k) {
-        if (axes[k] < 0) continue;
-        int b = 1;
-        while (b * 2 <= target[k] && R % (b * 2) == 0) b *= 2;
-        t->B[axes[k]] = b;
-        R /= b;
-    }
-    t->B[axes[0]] *= R;                             // what is left goes on p_{d-1} (q_1 for d = 1)
-    t->tpr = tpr;
-    t->rows = 1;
-    for (int ax = 0; ax < 5; ++ax) {
-        t->nb[ax] = ax < NR ? (n[ax] + t->B[ax] - 1) / t->B[ax] : 1;
-        t->rows *= t->B[ax];
-    }
-    return true;
-}
-
 template <typename T, int D, int DEPTH, int M32, int V, int NT, int MINB, bool PF = false,
-          bool QST = false, bool ES = false>
+          bool QST = false, int ES = 0>
 static void launch_vec(const StageArgs<T> &a, int batch, cudaStream_t s) {
     const int nthr = a.g.P / V;
     auto kern = stage_vec_kernel<T, D, DEPTH, V, NT, MINB, M32, PF, QST, ES>;
@@ -106,14 +65,6 @@ static void launch_vec(const StageArgs<T> &a, int batch, cudaStream_t s) {
         }
     }
     kern<<<dim3((nthr + NT - 1) / NT, batch), NT, smem, s>>>(a);
-}
-
-template <typename T, int D, int DEPTH, int M32, int NT, int MINB, bool ES = false>
-static void launch_tile(const StageArgs<T> &a, const RowTile &t, int batch, cudaStream_t s) {
-    long long blocks = 1;
-    for (int ax = 0; ax < 2 * D - 1; ++ax) blocks *= t.nb[ax];
-    stage_tile_kernel<T, D, DEPTH, 4, NT, MINB, M32, ES>
-        <<<dim3((unsigned)blocks, batch), NT, 0, s>>>(a, t);
 }
 
 constexpr int kBulkNT = 128, kBulkTP = kBulkNT * 4;
@@ -154,8 +105,6 @@ static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int varia
         return;
     }
     if constexpr (tunable(sizeof(T), D, DEPTH) && M32 == M) {
-        RowTile t;
-        const bool tiled = row_tile(variant, D, a.g.n, &t);
         switch (variant) {
         case 1: launch_vec<T, D, DEPTH, M32, 2, 256, MINB / 2>(a, batch, s); return;
         case 2: launch_vec<T, D, DEPTH, M32, 2, 128, 6>(a, batch, s); return;
@@ -166,18 +115,12 @@ static void launch_stage_m(const StageArgs<T> &a, int batch, bool vec, int varia
         case 9: launch_vec<T, D, DEPTH, M32, 4, 128, 4, false, true>(a, batch, s); return;
         case 10: launch_vec<T, D, DEPTH, M32, 4, 128, 3>(a, batch, s); return;
         case 11: launch_vec<T, D, DEPTH, M32, 4, 128, 2>(a, batch, s); return;
-        case 12:
-        case 13:
-        case 14:
-            if (tiled) { launch_tile<T, D, DEPTH, M32, 128, 4>(a, t, batch, s); return; }
-            break;
-        case 15:
-            if (tiled) { launch_tile<T, D, DEPTH, M32, 256, 2>(a, t, batch, s); return; }
-            break;
-        case 16: launch_vec<T, D, DEPTH, M32, 4, 128, 4, false, false, true>(a, batch, s); return;
-        case 17:
-            if (tiled) { launch_tile<T, D, DEPTH, M32, 128, 4, true>(a, t, batch, s); return; }
-            break;
+        case 12: launch_vec<T, D, DEPTH, M32, 4, 128, 5, false, false, 2>(a, batch, s); return;
+        case 13: launch_vec<T, D, DEPTH, M32, 4, 128, 5, false, false, 1>(a, batch, s); return;
+        case 14: launch_vec<T, D, DEPTH, M32, 2, 128, 8, false, false, 1>(a, batch, s); return;
+        case 15: launch_vec<T, D, DEPTH, M32, 4, 256, 2, false, false, 1>(a, batch, s); return;
+        case 16: launch_vec<T, D, DEPTH, M32, 4, 128, 4, false, false, 1>(a, batch, s); return;
+        case 17: launch_vec<T, D, DEPTH, M32, 4, 128, 4, false, false, 2>(a, batch, s); return;
         case 4:
         case 5:
             if constexpr (D == 2) {
