@@ -45,8 +45,10 @@ ELEM_ACCESSES_TEXTBOOK = 16           # the three-array k1..k4 form: 3 + 5 + 5 +
 # points per thread, threads per block, minimum resident blocks per SM), as in stage_launch.cuh
 STAGE_SHAPES = {0: (2, 128, 8), 1: (2, 256, 4), 2: (2, 128, 6), 3: (4, 128, 4), 4: (4, 128, 4), 5: (4, 128, 4),
                 6: (4, 256, 2), 7: (4, 64, 8), 8: (4, 128, 4),
-                9: (4, 128, 4), 10: (4, 128, 3), 11: (4, 128, 2), 12: (4, 128, 4), 13: (4, 128, 4),
-                14: (4, 128, 4), 15: (4, 256, 2), 16: (4, 128, 4), 17: (4, 128, 4)}
+                9: (4, 128, 4), 10: (4, 128, 3), 11: (4, 128, 2), 12: (4, 128, 5), 13: (4, 128, 5),
+                14: (2, 128, 8), 15: (4, 256, 2), 16: (4, 128, 4), 17: (4, 128, 4)}
+# early-store mode of each shape: 0 none, 1 storage order, 2 the open-accumulator order
+STAGE_ES = {12: 2, 13: 1, 14: 1, 15: 1, 16: 1, 17: 2}
 
 
 def parse():
@@ -265,10 +267,8 @@ def stage_kernel_name(variant: int, M: int = 15) -> str:
         return "stage_bulk_kernel<4, 128>"
     if variant == 5:
         return "stage_cpasync_kernel<4, 128>"
-    if variant in (12, 13, 14, 15, 17):
-        return "stage_tile_kernel<float, 2, 4, 4, %d, %d, %d, %s>" % (NT, MINB, M, b(variant == 17))
-    return "stage_vec_kernel<float, 2, 4, %d, %d, %d, %d, %s, %s, %s>" % (
-        V, NT, MINB, M, b(variant == 8), b(variant == 9), b(variant == 16))
+    return "stage_vec_kernel<float, 2, 4, %d, %d, %d, %d, %s, %s, %d>" % (
+        V, NT, MINB, M, b(variant == 8), b(variant == 9), STAGE_ES.get(variant, 0))
 
 
 def run_ours(args, rank, world, local, pg):

@@ -92,6 +92,11 @@ typedef struct {
                         /* then the bf16 members, each [grid] as above                          */
     int truncation;     /* 0: members with n_1+..+n_d <= depth (the tier sum; the only rule    */
                         /* built); 1 (max_s n_s <= depth) is rejected with CHFPE_EINVAL        */
+    int p_basis;        /* momenta: 0 = the uniform p grid of chfpe_grid; 1 = Hermite functions */
+                        /* (Sec. III A, Appendix A): grid.np[s] = K_s functions psi_0..psi_K-1 */
+                        /* of width sqrt(2 m_s kT), pmin/pmax unused; states then hold the    */
+                        /* coefficients [member][q_1..q_d][k_1..k_d], k_d fastest, in the     */
+                        /* ladder form of Eq. HEOM2FP-H (single handles, plain storage)        */
 } chfpe_options;
 
 /* Create a handle for one model on one grid.  Validates the structs, builds the coefficient

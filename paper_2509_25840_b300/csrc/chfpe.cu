@@ -4,6 +4,7 @@
 #include "../../include/chfpe.h"
 #include "kernels.cuh"
 #include "stage_launch.cuh"
+#include "hermite.cuh"
 #include "persistent.cuh"
 
 #include <cuda_runtime.h>
@@ -53,6 +54,7 @@ struct chfpe_handle {
     chfpe_grid grid;
     chfpe_options opts;
     int d = 0, depth = 0, M = 0, prec = 32;
+    int basis = 0;              // 0: momenta on a uniform grid; 1: Hermite functions (np = K_s)
     int P = 0, Pp = 0, NQ = 0;
     int n[6] = {0}, st[6] = {0};
     double lo[6] = {0}, h[6] = {0};
@@ -167,6 +169,34 @@ static StageArgs<T> stage_args(const chfpe_handle *h) {
     return a;
 }
 
+// Stage arguments of the Hermite-representation kernel (hermite.cuh)
+template <typename T>
+static HStageArgs<T> hstage_args(const chfpe_handle *h) {
+    HStageArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.state_bytes = (long long)h->state * sizeof(T);
+    HGeo<T> &g = a.g;
+    g.P = h->P;
+    g.NQ = h->NQ;
+    g.Pk = h->Pp;
+    for (int i = 0; i < 6; ++i) { g.n[i] = h->n[i]; g.st[i] = h->st[i]; }
+    if (sizeof(T) == 8) g.Fh = (const T *)h->F_d; else g.Fh = (const T *)h->F_f;
+    const chfpe_model &m = h->model;
+    for (int s = 0; s < h->d; ++s) {
+        const double smkT = std::sqrt(m.m[s] * m.kT);
+        g.cq[s] = (T)(smkT / m.m[s] / (60.0 * h->h[s]));
+        g.qlo[s] = (T)h->lo[s];
+        g.qh[s] = (T)h->h[s];
+        g.VLL[s] = (T)m.V_LL[s];
+        g.VSL[s] = (T)m.V_SL[s];
+        g.gam[s] = (T)m.gamma[s];
+        g.lk[s] = (T)(1.0 / smkT);
+        const double c = m.zeta[s] * m.gamma[s] * m.m[s] * m.kT;
+        for (int k = 0; k < kMaxDepth + 2; ++k) g.link[s][k] = (T)std::sqrt(k * c);
+    }
+    return a;
+}
+
 // BF16 storage of deep tiers is compiled for these (d, depth, first bf16 member) combinations
 // (FP32 path only): two modes, depth 4, tiers 3-4 (9 of 15 members); three modes, depth 2,
 // tier 2 (6 of 10 members).
@@ -201,6 +231,18 @@ static bool launch_stage(const chfpe_handle *h, const StageArgs<T> &a, int batch
 template <typename T>
 static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *out, double c,
                           int batch) {
+    if (h->basis) {
+        HStageArgs<T> a = hstage_args<T>(h);
+        a.in = (const char *)in;
+        a.y = (const char *)y;
+        a.out = (char *)out;
+        a.c = (T)c;
+        if (!launch_hstage<T>(h->d, h->depth, a, batch, h->stream))
+            return fail(CHFPE_EINVAL, "unsupported (d, depth)");
+        CK(cudaGetLastError());
+        ++h->launches;
+        return CHFPE_OK;
+    }
     StageArgs<T> a = stage_args<T>(h);
     a.in = (const char *)in;
     a.y = (const char *)y;
@@ -375,7 +417,10 @@ static ModelDev model_dev(const chfpe_handle *h) {
         md.nq[s] = h->n[s];
         md.qlo[s] = h->lo[s];
         md.qh[s] = h->h[s];
-        md.inv60hp[s] = 1.0 / (60.0 * h->h[h->d + s]);
+        // the force table holds dU/dq_s / (60 h_ps) for grid momenta and the ladder coefficient
+        // dU/dq_s / (2 sqrt(m_s kT)) of D+-_s for Hermite momenta
+        md.inv60hp[s] = h->basis ? 1.0 / (2.0 * std::sqrt(h->model.m[s] * h->model.kT))
+                                 : 1.0 / (60.0 * h->h[h->d + s]);
     }
     return md;
 }
@@ -447,6 +492,30 @@ static chfpe_status observe(chfpe_handle *h, const void *states, int batch, doub
 template <typename T>
 static chfpe_status insert_t(chfpe_handle *h, const chfpe_optical *X, const void *in,
                              long long in_state, void *out, int batch) {
+    if (h->basis) {
+        HInsertArgs<T> a;
+        memset(&a, 0, sizeof(a));
+        a.in = (const char *)in;
+        a.out = (char *)out;
+        a.in_state = in_state;
+        a.out_state = h->state_bytes;
+        a.P = h->P;
+        a.M = h->M;
+        a.d = h->d;
+        a.Pk = h->Pp;
+        for (int i = 0; i < 6; ++i) { a.n[i] = h->n[i]; a.st[i] = h->st[i]; }
+        for (int s = 0; s < h->d; ++s) {
+            a.qlo[s] = (T)h->lo[s];
+            a.qh[s] = (T)h->h[s];
+            a.lin[s] = (T)X->lin[s];
+            for (int b = 0; b < h->d; ++b) a.quad[s][b] = (T)(0.5 * (X->quad[s][b] + X->quad[b][s]));
+            a.lk[s] = (T)(1.0 / std::sqrt(h->model.m[s] * h->model.kT));
+        }
+        hinsert_kernel<T><<<dim3((h->P + 255) / 256, batch), 256, 0, h->stream>>>(a);
+        CK(cudaGetLastError());
+        ++h->launches;
+        return CHFPE_OK;
+    }
     InsertArgs<T> a;
     memset(&a, 0, sizeof(a));
     a.in = (const char *)in;
@@ -514,6 +583,21 @@ static double spectral_bound(const chfpe_handle *h) {
             if (std::fabs(F) > Fmax[s]) Fmax[s] = std::fabs(F);
         }
     }
+    if (h->basis) {
+        // Hermite momenta: per mode the ladder block (entries sqrt(k) D+-, a tridiagonal in k) is
+        // bounded by 2 sqrt(K-1) max|D+-|, |D+-| <= max|dU/dq|/(2 sqrt(mkT)) + sqrt(mkT)/m K/h_q;
+        // the links by 2 sqrt(depth c) max|V'| sqrt(K) / sqrt(mkT)
+        for (int s = 0; s < h->d; ++s) {
+            const double hq = h->h[s], Kh = h->n[h->d + s], smkT = std::sqrt(m.m[s] * m.kT);
+            const double qmax = std::fmax(std::fabs(h->lo[s]), std::fabs(h->lo[s] + (h->n[s] - 1) * hq));
+            const double Vmax = std::fabs(m.V_LL[s]) + std::fabs(m.V_SL[s]) * qmax;
+            const double c = m.zeta[s] * m.gamma[s] * m.m[s] * m.kT;
+            rho += 2.0 * std::sqrt(std::fmax(Kh - 1.0, 0.0)) * (Fmax[s] / (2.0 * smkT) + smkT / m.m[s] * K / hq);
+            rho += 2.0 * std::sqrt(h->depth * c) * Vmax * std::sqrt(Kh) / smkT;
+            gmax = std::fmax(gmax, m.gamma[s]);
+        }
+        return rho + h->depth * gmax;
+    }
     for (int s = 0; s < h->d; ++s) {
         const double hq = h->h[s], hp = h->h[h->d + s];
         const double pmax = std::fmax(std::fabs(h->lo[h->d + s]), std::fabs(h->lo[h->d + s] + (h->n[h->d + s] - 1) * hp));
@@ -534,6 +618,12 @@ static chfpe_status validate(const chfpe_model *m, const chfpe_grid *g, const ch
     for (int s = 0; s < m->nmodes; ++s) {
         if (!(m->m[s] > 0) || !is_fin(m->m[s])) return fail(CHFPE_EINVAL, "masses must be positive");
         if (m->zeta[s] < 0 || m->gamma[s] < 0) return fail(CHFPE_EINVAL, "zeta, gamma must be >= 0");
+        if (o->p_basis == 1) {
+            if (g->nq[s] < 7 || g->np[s] < 1 || g->np[s] > 256)
+                return fail(CHFPE_EINVAL, "at least 7 q points per axis and 1..256 Hermite functions");
+            if (!(g->qmax[s] > g->qmin[s])) return fail(CHFPE_EINVAL, "grid bounds must satisfy min < max");
+            continue;
+        }
         if (g->nq[s] < 7 || g->np[s] < 7) return fail(CHFPE_EINVAL, "at least 7 points per axis");
         if (!(g->qmax[s] > g->qmin[s]) || !(g->pmax[s] > g->pmin[s]))
             return fail(CHFPE_EINVAL, "grid bounds must satisfy min < max");
@@ -543,6 +633,9 @@ static chfpe_status validate(const chfpe_model *m, const chfpe_grid *g, const ch
     if (o->precision != 32 && o->precision != 64) return fail(CHFPE_EINVAL, "precision must be 32 or 64");
     if (o->truncation != 0)
         return fail(CHFPE_EINVAL, "truncation: only 0 (n_1 + .. + n_d <= depth) is built");
+    if (o->p_basis != 0 && o->p_basis != 1) return fail(CHFPE_EINVAL, "p_basis must be 0 (grid) or 1 (Hermite)");
+    if (o->p_basis == 1 && o->bf16_tier > 0)
+        return fail(CHFPE_EINVAL, "bf16 tiers are built for grid momenta only");
     if (!(o->dt > 0) || !is_fin(o->dt)) return fail(CHFPE_EINVAL, "dt must be positive");
     if (o->max_batch < 0 || o->max_batch > 65535) return fail(CHFPE_EINVAL, "max_batch must be in 0..65535");
     long long P = 1;
@@ -606,14 +699,20 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
     h->prec = opts->precision;
     h->esize = h->prec == 64 ? 8 : 4;
     h->dt = opts->dt;
+    h->basis = opts->p_basis;
     const int d = h->d;
     for (int s = 0; s < d; ++s) {
         h->n[s] = grid->nq[s];
         h->n[d + s] = grid->np[s];
         h->lo[s] = grid->qmin[s];
-        h->lo[d + s] = grid->pmin[s];
         h->h[s] = (grid->qmax[s] - grid->qmin[s]) / (grid->nq[s] - 1);
-        h->h[d + s] = (grid->pmax[s] - grid->pmin[s]) / (grid->np[s] - 1);
+        if (h->basis) {            // Hermite indices k = 0..K_s-1: no coordinate, unit weight
+            h->lo[d + s] = 0.0;
+            h->h[d + s] = 1.0;
+        } else {
+            h->lo[d + s] = grid->pmin[s];
+            h->h[d + s] = (grid->pmax[s] - grid->pmin[s]) / (grid->np[s] - 1);
+        }
     }
     h->st[2 * d - 1] = 1;
     for (int ax = 2 * d - 2; ax >= 0; --ax) h->st[ax] = h->st[ax + 1] * h->n[ax + 1];
@@ -708,10 +807,20 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
     if (e) { chfpe_destroy(h); return fail(CHFPE_ECUDA, cudaGetErrorString(e)); }
     setup_fields_kernel<<<(h->NQ + 127) / 128, 128, 0, h->stream>>>(model_dev(h), h->NQ, h->U_d,
                                                                      h->F_d, h->F_f);
-    dim3 gw((h->wp_ld + 127) / 128, d);
-    setup_wp_kernel<<<gw, 128, 0, h->stream>>>(d, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
-                                               0.5 / model->kT, h->wp, h->wp_ld);
-    e = cudaGetLastError();
+    if (h->basis) {
+        // integral exp(-p^2/4mkT) psi_k(p) dp = sqrt(a sqrt(pi)) for k = 0, else 0 (a = sqrt(2mkT))
+        std::vector<double> wph((size_t)3 * h->wp_ld, 0.0);
+        for (int s = 0; s < d; ++s)
+            wph[(size_t)s * h->wp_ld] = std::sqrt(std::sqrt(2.0 * model->m[s] * model->kT) * std::sqrt(M_PI));
+        e = cudaMemcpyAsync(h->wp, wph.data(), wph.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            h->stream);
+        if (!e) e = cudaStreamSynchronize(h->stream);
+    } else {
+        dim3 gw((h->wp_ld + 127) / 128, d);
+        setup_wp_kernel<<<gw, 128, 0, h->stream>>>(d, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
+                                                   0.5 / model->kT, h->wp, h->wp_ld);
+    }
+    if (!e) e = cudaGetLastError();
     if (!e) e = cudaStreamSynchronize(h->stream);
     if (e) { chfpe_destroy(h); return fail(CHFPE_ECUDA, cudaGetErrorString(e)); }
     if (!borrowed && (st = autotune(h))) { chfpe_destroy(h); return st; }
@@ -733,7 +842,7 @@ static chfpe_status autotune(chfpe_handle *h) {
     }
     const int npd = h->n[2 * h->d - 1];
     if (h->prec != 32 || h->M32 != h->M || !tunable(4, h->d, h->depth) || h->force_scalar ||
-        npd % kVec != 0)
+        npd % kVec != 0 || h->basis)
         return CHFPE_OK;
     char *in = (char *)(h->ba ? h->ba : h->ca);
     char *out = (char *)(h->bb ? h->bb : h->cb);
@@ -931,9 +1040,21 @@ extern "C" chfpe_status chfpe_equilibrate(chfpe_handle *h, long max_steps, doubl
     // g^(0) = exp(-H/2kT) / Z, other members zero
     CK(cudaMemsetAsync(y, 0, n * 8, h->stream));
     const int nblk = 296;
-    boltzmann_kernel<256><<<nblk, 256, 0, h->stream>>>(y, h->P, h->Pp, h->d, h->U_d, h->np_d,
-                                                        h->plo_d, h->ph_d, h->inv2m_d,
-                                                        0.5 / h->model.kT, h->partial, nblk);
+    if (h->basis) {
+        // c^(0)_0 = exp(-U/2kT) prod_s sqrt(a_s sqrt(pi)) / sqrt(2 pi m_s kT) / Z_q (the p-integral
+        // of the Boltzmann factor taken exactly; Z_q on the q nodes)
+        double cnorm = 1.0;
+        for (int s = 0; s < h->d; ++s) {
+            const double mkT = h->model.m[s] * h->model.kT;
+            cnorm *= std::sqrt(std::sqrt(2.0 * mkT) * std::sqrt(M_PI)) / std::sqrt(2.0 * M_PI * mkT);
+        }
+        hboltzmann_kernel<256><<<nblk, 256, 0, h->stream>>>(y, h->P, h->Pp, h->U_d,
+                                                             0.5 / h->model.kT, cnorm, h->partial, nblk);
+    } else {
+        boltzmann_kernel<256><<<nblk, 256, 0, h->stream>>>(y, h->P, h->Pp, h->d, h->U_d, h->np_d,
+                                                            h->plo_d, h->ph_d, h->inv2m_d,
+                                                            0.5 / h->model.kT, h->partial, nblk);
+    }
     double vol = 1.0;
     for (int ax = 0; ax < 2 * h->d; ++ax) vol *= h->h[ax];
     scale_by_sum_kernel<<<296, 256, 0, h->stream>>>(y, h->P, h->partial, nblk, vol);
@@ -1072,7 +1193,7 @@ static chfpe_status persistent_dispatch(chfpe_handle *h, const PersistArgs &p, b
 
 static bool persistent_ok(const chfpe_handle *h, int batch, int nsamples) {
     const long long chunks = (h->P + kObsChunk - 1) / kObsChunk;   // partial sums per state
-    return h->use_persistent && !h->time_stages && h->M32 == h->M && nsamples >= 2 &&
+    return h->use_persistent && !h->time_stages && h->M32 == h->M && nsamples >= 2 && !h->basis &&
            persistent_config(h->d, h->depth) && (double)batch * (double)h->state <= kPersistCells &&
            chunks * batch <= h->partial_cap;
 }
@@ -1319,6 +1440,7 @@ static EqHeader make_header(const chfpe_handle *h) {
     hd.d = h->d;
     hd.depth = h->depth;
     hd.M = h->M;
+    hd.pad = h->basis;
     for (int s = 0; s < 3; ++s) {
         hd.nq[s] = s < h->d ? h->grid.nq[s] : 0;
         hd.np[s] = s < h->d ? h->grid.np[s] : 0;
@@ -1660,6 +1782,7 @@ extern "C" chfpe_status chfpe_create_batch(int n, const chfpe_model *models, con
     if (!out || !models || !grids || !opts) return fail(CHFPE_EINVAL, "null argument");
     *out = nullptr;
     if (n < 1) return fail(CHFPE_EINVAL, "n must be >= 1");
+    if (opts->p_basis != 0) return fail(CHFPE_EINVAL, "batches are built for grid momenta only");
     for (int i = 0; i < n; ++i) {
         chfpe_status st = validate(&models[i], &grids[i], opts);
         if (st) return fail(st, "instance " + std::to_string(i) + ": " + g_err);

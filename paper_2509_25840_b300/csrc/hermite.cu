@@ -1,0 +1,39 @@
+// hermite.cu -- launchers of the Hermite-representation stage kernel (hermite.cuh) for every
+// compiled (modes, depth), FP32 and FP64, in a translation unit of their own.
+#include "hermite.cuh"
+
+namespace chfpe {
+
+namespace {
+constexpr int kHNT = 128;
+
+template <typename T, int D, int K>
+void launch_one(const HStageArgs<T> &a, int batch, cudaStream_t s) {
+    hstage_kernel<T, D, K, kHNT><<<dim3((a.g.P + kHNT - 1) / kHNT, batch), kHNT, 0, s>>>(a);
+}
+
+template <typename T>
+bool launch_any(int d, int depth, const HStageArgs<T> &a, int batch, cudaStream_t s) {
+    switch (d * 16 + depth) {
+#define HCASE(D_, K_) case (D_ * 16 + K_): launch_one<T, D_, K_>(a, batch, s); return true;
+        HCASE(1, 0) HCASE(1, 1) HCASE(1, 2) HCASE(1, 3) HCASE(1, 4) HCASE(1, 5) HCASE(1, 6)
+        HCASE(1, 7) HCASE(1, 8)
+        HCASE(2, 0) HCASE(2, 1) HCASE(2, 2) HCASE(2, 3) HCASE(2, 4) HCASE(2, 5)
+        HCASE(3, 0) HCASE(3, 1) HCASE(3, 2) HCASE(3, 3)
+#undef HCASE
+    default: return false;
+    }
+}
+}  // namespace
+
+template <>
+bool launch_hstage<float>(int d, int depth, const HStageArgs<float> &a, int batch, cudaStream_t s) {
+    return launch_any<float>(d, depth, a, batch, s);
+}
+
+template <>
+bool launch_hstage<double>(int d, int depth, const HStageArgs<double> &a, int batch, cudaStream_t s) {
+    return launch_any<double>(d, depth, a, batch, s);
+}
+
+}  // namespace chfpe

@@ -1,0 +1,198 @@
+// hermite.cuh -- the CHFPE hot path with the momenta in Hermite functions (Sec. III A, Appendix A,
+// Eq. HEOM2FP-H): every member is g^(n)(q,p) = sum_k c^(n)_k(q) prod_s psi_{k_s}(p_s), psi_j the
+// orthonormal Hermite functions of width a_s = sqrt(2 m_s kT) (the paper's expansion, whose
+// prefactor psi_0(p) exp(-U/2kT) is the exp(-H/2kT) of the symmetrised members), stored
+// [batch][member][q_1..q_d][k_1..k_d], k_d fastest.  The momentum derivatives of the grid kernels
+// become ladder couplings; only the q axes carry a stencil:
+//   dc^(n)_k/dt = sum_s [ sqrt(k_s+1) D+_s c^(n)_{k+e_s} - sqrt(k_s) D-_s c^(n)_{k-e_s} ]
+//               - sum_s n_s gamma_s c^(n)_k
+//               - sum_s sqrt((n_s+1) c_s) V_s' sqrt(k_s) / sqrt(m_s kT) c^(n+e_s)_{k-e_s}
+//               + sum_s sqrt(n_s c_s)     V_s' sqrt(k_s+1) / sqrt(m_s kT) c^(n-e_s)_{k+e_s}
+//   D+-_s = dU/dq_s / (2 sqrt(m_s kT)) -+ (sqrt(m_s kT) / m_s) d/dq_s
+// (c_s = zeta_s gamma_s m_s kT; coefficients with k_s outside [0, K_s) are zero; d/dq_s the
+// 6th-order central difference with zero values outside the q-grid).  The insertion X^x raises
+// k:  (X^x c)_k = -sum_s dX/dq_s sqrt(k_s) / sqrt(m_s kT) c_{k-e_s};  only c^(0)_0 reaches the
+// observable.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace chfpe {
+
+template <typename T>
+struct HGeo {
+    int P, NQ, Pk;              // points per member (q x k), q points, k points per q point
+    int n[6], st[6];            // axis sizes and strides: q_1..q_d, k_1..k_d
+    const T *Fh;                // [D][NQ]: dU/dq_s / (2 sqrt(m_s kT))
+    T cq[3];                    // sqrt(m_s kT) / m_s / (60 h_qs)
+    T qlo[3], qh[3];
+    T VLL[3], VSL[3], gam[3];
+    T lk[3];                    // 1 / sqrt(m_s kT)
+    T link[3][kMaxDepth + 2];   // sqrt(k c_s)
+};
+
+template <typename T>
+struct HStageArgs {
+    const char *in;             // stencil input, batch of states
+    const char *y;              // base states or nullptr: out = c * M in
+    char *out;
+    long long state_bytes;
+    T c;
+    HGeo<T> g;
+};
+
+// 45 (f+1 - f-1) - 9 (f+2 - f-2) + (f+3 - f-3) along q axis `s` of the point x (q index i)
+template <typename T>
+__device__ __forceinline__ T hstencil(const T *__restrict__ f, int x, int i, int N, int st) {
+    const T p1 = (i + 1 < N) ? __ldg(f + x + st) : T(0);
+    const T m1 = (i >= 1) ? __ldg(f + x - st) : T(0);
+    const T p2 = (i + 2 < N) ? __ldg(f + x + 2 * st) : T(0);
+    const T m2 = (i >= 2) ? __ldg(f + x - 2 * st) : T(0);
+    const T p3 = (i + 3 < N) ? __ldg(f + x + 3 * st) : T(0);
+    const T m3 = (i >= 3) ? __ldg(f + x - 3 * st) : T(0);
+    return T(45) * (p1 - m1) - T(9) * (p2 - m2) + (p3 - m3);
+}
+
+// one RK4 stage, one thread per (q, k) point for every member (gather form: each output reads the
+// q-stencils of its k +- e_s neighbours and the link values of its member neighbours)
+template <typename T, int D, int DEPTH, int NT>
+__global__ void __launch_bounds__(NT) hstage_kernel(const HStageArgs<T> a) {
+    constexpr MemberTable<D, DEPTH> tab{};
+    constexpr int M = MemberTable<D, DEPTH>::M;
+    const HGeo<T> &g = a.g;
+    const int x = blockIdx.x * NT + threadIdx.x;
+    if (x >= g.P) return;
+    const long long boff = (long long)blockIdx.y * a.state_bytes;
+    const T *in = reinterpret_cast<const T *>(a.in + boff);
+    T *out = reinterpret_cast<T *>(a.out + boff);
+    const T *y = a.y ? reinterpret_cast<const T *>(a.y + boff) : nullptr;
+
+    int idx[2 * D];
+    {
+        int r = x;
+#pragma unroll
+        for (int ax = 2 * D - 1; ax >= 0; --ax) {
+            idx[ax] = r % g.n[ax];
+            r /= g.n[ax];
+        }
+    }
+    const int qlin = x / g.Pk;
+    T F[D], Vl[D], sk[D], sk1[D];
+    bool hp[D], hm[D];
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+        F[s] = __ldg(g.Fh + s * g.NQ + qlin);
+        const T q = g.qlo[s] + T(idx[s]) * g.qh[s];
+        Vl[s] = (g.VLL[s] + g.VSL[s] * q) * g.lk[s];
+        const int k = idx[D + s];
+        sk[s] = sqrt(T(k));
+        sk1[s] = sqrt(T(k + 1));
+        hp[s] = k + 1 < g.n[D + s];
+        hm[s] = k >= 1;
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const T *c = in + (long long)m * g.P;
+        T gm = T(0);
+#pragma unroll
+        for (int s = 0; s < D; ++s) gm += T(tab.n[m][s]) * g.gam[s];
+        T acc = -gm * __ldg(c + x);
+#pragma unroll
+        for (int s = 0; s < D; ++s) {
+            const int sk_st = g.st[D + s];
+            if (hp[s]) {             // sqrt(k+1) D+ c_{k+e_s}
+                const int xp = x + sk_st;
+                const T dq = hstencil<T>(c, xp, idx[s], g.n[s], g.st[s]);
+                acc += sk1[s] * (F[s] * __ldg(c + xp) - g.cq[s] * dq);
+            }
+            if (hm[s]) {             // - sqrt(k) D- c_{k-e_s}
+                const int xm = x - sk_st;
+                const T dq = hstencil<T>(c, xm, idx[s], g.n[s], g.st[s]);
+                acc -= sk[s] * (F[s] * __ldg(c + xm) + g.cq[s] * dq);
+            }
+            if (tab.up[m][s] >= 0 && hm[s]) {
+                const T *cu = in + (long long)tab.up[m][s] * g.P;
+                acc -= g.link[s][tab.n[m][s] + 1] * Vl[s] * sk[s] * __ldg(cu + x - sk_st);
+            }
+            if (tab.dn[m][s] >= 0 && hp[s]) {
+                const T *cd = in + (long long)tab.dn[m][s] * g.P;
+                acc += g.link[s][tab.n[m][s]] * Vl[s] * sk1[s] * __ldg(cd + x + sk_st);
+            }
+        }
+        const long long o = (long long)m * g.P + x;
+        out[o] = y ? y[o] + a.c * acc : a.c * acc;
+    }
+}
+
+template <typename T>
+struct HInsertArgs {
+    const char *in;
+    char *out;
+    long long in_state, out_state;   // batch strides in bytes (in_state may be 0: one input)
+    int P, M, d, Pk;
+    int n[6], st[6];
+    T qlo[3], qh[3];
+    T lin[3];
+    T quad[3][3];                    // symmetric part
+    T lk[3];                         // 1 / sqrt(m_s kT)
+};
+
+// X^x on every member: out_k = -sum_s dX/dq_s sqrt(k_s) / sqrt(m_s kT) in_{k-e_s}
+template <typename T>
+__global__ void __launch_bounds__(256) hinsert_kernel(const HInsertArgs<T> a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= a.P) return;
+    const T *in = reinterpret_cast<const T *>(a.in + (long long)blockIdx.y * a.in_state);
+    T *out = reinterpret_cast<T *>(a.out + (long long)blockIdx.y * a.out_state);
+    const int d = a.d;
+    int idx[6];
+    int r = x;
+    for (int ax = 2 * d - 1; ax >= 0; --ax) {
+        idx[ax] = r % a.n[ax];
+        r /= a.n[ax];
+    }
+    T G[3];
+    for (int s = 0; s < d; ++s) {
+        T gs = a.lin[s];
+        for (int b = 0; b < d; ++b) gs += a.quad[s][b] * (a.qlo[b] + T(idx[b]) * a.qh[b]);
+        G[s] = gs * a.lk[s] * sqrt(T(idx[d + s]));
+    }
+    for (int m = 0; m < a.M; ++m) {
+        const T *c = in + (long long)m * a.P;
+        T v = T(0);
+        for (int s = 0; s < d; ++s)
+            if (idx[d + s] >= 1) v -= G[s] * __ldg(c + x - a.st[d + s]);
+        out[(long long)m * a.P + x] = v;
+    }
+}
+
+// equilibrium sample: c^(0)_0(q) = cnorm exp(-U(q)/2kT) (the caller divides by the q-volume
+// times sum exp(-U/kT), accumulated here in partial[]), every other k and member 0
+template <int NT>
+__global__ void __launch_bounds__(NT) hboltzmann_kernel(double *c0, int P, int Pk,
+                                                        const double *Uq, double inv2kT,
+                                                        double cnorm, double *partial, int nblk) {
+    double sum = 0.0;
+    for (int x = blockIdx.x * NT + threadIdx.x; x < P; x += nblk * NT) {
+        const int qlin = x / Pk;
+        const bool k0 = (x - qlin * Pk) == 0;
+        const double e = exp(-Uq[qlin] * inv2kT);
+        c0[x] = k0 ? cnorm * e : 0.0;
+        if (k0) sum += e * e;
+    }
+    sum = block_sum<NT>(sum);
+    if (threadIdx.x == 0) partial[blockIdx.x] = sum;
+}
+
+// One RK4 stage of `batch` Hermite-representation states of a D-mode hierarchy of the given
+// depth; false for a combination that is not compiled.  Specialised in hermite.cu.
+template <typename T>
+bool launch_hstage(int d, int depth, const HStageArgs<T> &a, int batch, cudaStream_t s);
+template <>
+bool launch_hstage<float>(int d, int depth, const HStageArgs<float> &a, int batch, cudaStream_t s);
+template <>
+bool launch_hstage<double>(int d, int depth, const HStageArgs<double> &a, int batch, cudaStream_t s);
+
+}  // namespace chfpe
