@@ -28,7 +28,12 @@ Parity status per function (what pins it; the pins live in ``tests/test_oracle_p
                the vanishing third-order response of the harmonic / all-linear case
   h_*          (Hermite-function momenta, Appendix A) the antisymmetry of the ladder generator,
                Boltzmann stationarity, the Brownian closed form, the moment closure, and the
-               grid representation's responses on the same model
+               grid representation's responses on the same model; with qscheme = 1 (compact q
+               derivatives, Sec. III B) the Brownian closed form, Boltzmann stationarity and
+               convergence to the explicit scheme's limit
+  compact_deriv1d  exactness on polynomials of degree <= 6 away from the ends, the scheme's
+               closed-form Fourier symbol, the truncation-error constant against the explicit
+               stencil (1/9 of it), decay of the end effect at the rate of A's Green's function
 """
 from __future__ import annotations
 
@@ -69,6 +74,7 @@ class _Problem(ctypes.Structure):
         ("nq", ctypes.c_int * 3), ("np", ctypes.c_int * 3),
         ("qmin", ctypes.c_double * 3), ("qmax", ctypes.c_double * 3),
         ("pmin", ctypes.c_double * 3), ("pmax", ctypes.c_double * 3),
+        ("qscheme", ctypes.c_int),
     ]
 
 
@@ -96,6 +102,7 @@ def _load():
             lib.orc_dUdq.argtypes = [P, _DP, ctypes.c_int]
             lib.orc_dUdq.restype = ctypes.c_double
             lib.orc_deriv1d.argtypes = [ctypes.c_long, ctypes.c_double, _DP, _DP]
+            lib.orc_compact_deriv1d.argtypes = [ctypes.c_long, ctypes.c_double, _DP, _DP]
             lib.orc_rhs.argtypes = [P, _DP, _DP]
             lib.orc_rk4.argtypes = [P, _DP, ctypes.c_double, ctypes.c_long]
             lib.orc_insert.argtypes = [P, O, _DP, _DP]
@@ -139,9 +146,10 @@ def members(d: int, depth: int) -> np.ndarray:
 class Problem:
     """One model on one grid with one hierarchy depth, as the oracle sees it."""
 
-    def __init__(self, model, grid, depth: int):
+    def __init__(self, model, grid, depth: int, qscheme: int = 0):
         d = int(model.nmodes)
         s = _Problem()
+        s.qscheme = int(qscheme)
         s.d = d
         s.depth = int(depth)
         s.kT = float(model.kT)
@@ -215,6 +223,15 @@ def deriv1d(f, h: float) -> np.ndarray:
     f = np.ascontiguousarray(f, dtype=np.float64)
     out = np.empty_like(f)
     _load().orc_deriv1d(f.size, float(h), _p(f), _p(out))
+    return out
+
+
+def compact_deriv1d(f, h: float) -> np.ndarray:
+    """The compact sixth-order first derivative of Sec. III B (tridiagonal solve, zero values
+    outside the array; constants alpha = 1/3, a = 7/9, b = 1/36)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty_like(f)
+    _load().orc_compact_deriv1d(f.size, float(h), _p(f), _p(out))
     return out
 
 

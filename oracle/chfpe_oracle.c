@@ -36,8 +36,9 @@
  * discrete generator is antisymmetric minus a non-negative diagonal: no growing modes.  (The
  * same central differences applied to W^(n) itself give growing modes.)
  *
- * Discretisation (the paper's own compact scheme is replaced by an explicit one): every axis is
- * a uniform grid with both end points, derivatives are the 6th-order central difference
+ * Discretisation (on the p-grid representation the paper's compact scheme is replaced by an
+ * explicit one; the Hermite representation below offers both): every axis is a uniform grid
+ * with both end points, derivatives are the 6th-order central difference
  *   (D f)_i = [45 (f_{i+1}-f_{i-1}) - 9 (f_{i+2}-f_{i-2}) + (f_{i+3}-f_{i-3})] / (60 h)
  * with zero values outside the grid, the hierarchy is truncated at n_1+...+n_d <= depth, and
  * time stepping is the textbook classical Runge-Kutta method (k1..k4).
@@ -64,6 +65,8 @@ typedef struct {
     double zeta[3], gamma[3], V_LL[3], V_SL[3];
     int nq[3], np[3];
     double qmin[3], qmax[3], pmin[3], pmax[3];
+    int qscheme;         /* q-derivatives of the Hermite representation: 0 = the explicit
+                            6th-order central difference, 1 = the compact scheme of Sec. III B */
 } orc_problem;
 
 typedef struct {
@@ -264,6 +267,35 @@ void orc_deriv1d(long n, double h, const double *f, double *out)
         }
         out[i] = acc / (60.0 * h);
     }
+}
+
+/* Compact (Pade) first derivative of Sec. III B on a 1-D array: solve A f' = B f / h with
+ *   A = tridiag(alpha, 1, alpha)                 (first row 1, alpha; last row alpha, 1)
+ *   (B f)_i = a (f_{i+1} - f_{i-1}) + b (f_{i+2} - f_{i-2}),  zero values outside [0, n)
+ * alpha = 1/3, a = 7/9, b = 1/36: the sixth-order tridiagonal scheme of Lele (J. Comput. Phys.
+ * 103, 16 (1992)), whose interior consistency on f = x needs 2a + 4b = 1 + 2 alpha; the paper
+ * prints a = beta/2 = 7/18, which fails that condition, and the reading taken is a = 7/9 (the
+ * paper's beta = 14/9 halved).  The tridiagonal system is solved by forward elimination and
+ * back substitution (Thomas algorithm). */
+void orc_compact_deriv1d(long n, double h, const double *f, double *out)
+{
+    const double alpha = 1.0 / 3.0, a = 7.0 / 9.0, b = 1.0 / 36.0;
+    double *cp = malloc(sizeof(double) * (n > 0 ? n : 1));
+    for (long i = 0; i < n; ++i) {
+        double f1p = (i + 1 < n) ? f[i + 1] : 0.0, f1m = (i >= 1) ? f[i - 1] : 0.0;
+        double f2p = (i + 2 < n) ? f[i + 2] : 0.0, f2m = (i >= 2) ? f[i - 2] : 0.0;
+        out[i] = (a * (f1p - f1m) + b * (f2p - f2m)) / h;
+    }
+    /* forward elimination: row i becomes x_i + cp_i x_{i+1} = out_i */
+    for (long i = 0; i < n; ++i) {
+        double sub = (i >= 1) ? alpha : 0.0;
+        double sup = (i + 1 < n) ? alpha : 0.0;
+        double piv = 1.0 - ((i >= 1) ? sub * cp[i - 1] : 0.0);
+        cp[i] = sup / piv;
+        out[i] = (out[i] - ((i >= 1) ? sub * out[i - 1] : 0.0)) / piv;
+    }
+    for (long i = n - 2; i >= 0; --i) out[i] -= cp[i] * out[i + 1];
+    free(cp);
 }
 
 /* the same derivative along axis a of one member's field, at point x */
@@ -603,7 +635,8 @@ int orc_response2(const orc_problem *pr, const orc_optical *A, const orc_optical
  * out); (d/dp - p/2mkT) psi_k = -sqrt(k+1) psi_{k+1} / sqrt(mkT) is the raising operator the
  * Phi link and the insertion use, (d/dp + p/2mkT) the matching lowering operator.  Coefficients
  * with k_s outside [0, K_s) are zero (truncation).  d/dq_s is the same 6th-order central
- * difference with zero values outside the q-grid.
+ * difference with zero values outside the q-grid (qscheme 0), or the compact scheme of
+ * Sec. III B, orc_compact_deriv1d (qscheme 1).
  *
  * Layout: [member][q_1]..[q_d][k_1]..[k_d], k_d fastest; the orc_problem's np[s] holds K_s
  * (pmin/pmax are not used).
@@ -632,13 +665,49 @@ static double hcoef(const orc_geom *g, const double *C, int member, long x, cons
     return C[(long)member * g->P + x + dk * g->stride[g->d + s]];
 }
 
-/* d/dq_s of c^(i)_{k + dk e_s} at the point x (zero outside the q-grid and outside [0, K_s)) */
+/* d/dq_s of c^(i)_{k + dk e_s} at the point x (zero outside the q-grid and outside [0, K_s));
+ * Dpre == NULL: the explicit central difference; else Dpre[(s M + i) P + x] holds the compact
+ * derivatives (h_compact_derivs) */
 static double hderiv_q(const orc_geom *g, const double *C, int i, long x, const long *idx, int s,
-                       int dk)
+                       int dk, const double *Dpre)
 {
     long k = idx[g->d + s] + dk;
     if (k < 0 || k >= g->n[g->d + s]) return 0.0;
+    if (Dpre) return Dpre[((long)s * g->M + i) * g->P + x + dk * g->stride[g->d + s]];
     return deriv_axis(g, C + (long)i * g->P, x + dk * g->stride[g->d + s], idx, s);
+}
+
+/* the compact derivative (Sec. III B) of every member's coefficients along every q axis, line by
+ * line: D[(s M + i) P + x] = d/dq_s c^(i) at x.  NULL when out of memory. */
+static double *h_compact_derivs(const orc_geom *g, const double *C)
+{
+    const int d = g->d;
+    const long P = g->P;
+    double *D = malloc(sizeof(double) * d * g->M * P);
+    if (!D) return NULL;
+    int bad = 0;
+    for (int s = 0; s < d; ++s) {
+        const long n = g->n[s], st = g->stride[s];
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int i = 0; i < g->M; ++i) {
+            for (long x0 = 0; x0 < P; ++x0) {
+                if ((x0 / st) % n != 0) continue;      /* one line per start point q_s = q_min */
+                double *f = malloc(sizeof(double) * n), *df = malloc(sizeof(double) * n);
+                if (!f || !df) {
+                    free(f); free(df);
+#pragma omp atomic write
+                    bad = 1;
+                    continue;
+                }
+                for (long j = 0; j < n; ++j) f[j] = C[(long)i * P + x0 + j * st];
+                orc_compact_deriv1d(n, g->h[s], f, df);
+                for (long j = 0; j < n; ++j) D[((long)s * g->M + i) * P + x0 + j * st] = df[j];
+                free(f); free(df);
+            }
+        }
+    }
+    if (bad) { free(D); return NULL; }
+    return D;
 }
 
 int orc_h_rhs(const orc_problem *pr, const double *Cin, double *K)
@@ -648,6 +717,13 @@ int orc_h_rhs(const orc_problem *pr, const double *Cin, double *K)
     const int d = g.d;
     const long P = g.P;
     const double kT = pr->kT;
+    double *Dpre = NULL;
+    if (pr->qscheme == 1) {
+        Dpre = h_compact_derivs(&g, Cin);
+        if (!Dpre) return -3;
+    } else if (pr->qscheme != 0) {
+        return -1;
+    }
     int up[ORC_MAXM][ORC_MAXD], dn[ORC_MAXM][ORC_MAXD];
     for (int i = 0; i < g.M; ++i)
         for (int s = 0; s < d; ++s) {
@@ -673,8 +749,8 @@ int orc_h_rhs(const orc_problem *pr, const double *Cin, double *K)
                 /* sqrt(k+1) D+ c_{k+e_s} - sqrt(k) D- c_{k-e_s} */
                 const double cp = hcoef(&g, Cin, i, x, idx, s, +1);
                 const double cm = hcoef(&g, Cin, i, x, idx, s, -1);
-                const double dcp = hderiv_q(&g, Cin, i, x, idx, s, +1);
-                const double dcm = hderiv_q(&g, Cin, i, x, idx, s, -1);
+                const double dcp = hderiv_q(&g, Cin, i, x, idx, s, +1, Dpre);
+                const double dcm = hderiv_q(&g, Cin, i, x, idx, s, -1, Dpre);
                 val += sqrt(ks + 1.0) * (F / (2.0 * smkT) * cp - smkT / pr->m[s] * dcp);
                 val -= sqrt(ks) * (F / (2.0 * smkT) * cm + smkT / pr->m[s] * dcm);
                 /* hierarchy links */
@@ -692,6 +768,7 @@ int orc_h_rhs(const orc_problem *pr, const double *Cin, double *K)
             K[(long)i * P + x] = val;
         }
     }
+    free(Dpre);
     return 0;
 }
 
