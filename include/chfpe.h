@@ -97,6 +97,12 @@ typedef struct {
                         /* of width sqrt(2 m_s kT), pmin/pmax unused; states then hold the    */
                         /* coefficients [member][q_1..q_d][k_1..k_d], k_d fastest, in the     */
                         /* ladder form of Eq. HEOM2FP-H (single handles, plain storage)        */
+    int q_scheme;       /* q-derivatives with Hermite momenta: 0 = explicit 6th-order central   */
+                        /* stencil; 1 = the compact 6th-order scheme of Sec. III B (A f' = B f/h,*/
+                        /* alpha = 1/3, a = 7/9, b = 1/36, zero values outside the q-grid),     */
+                        /* tridiagonal systems solved by parallel cyclic reduction (Sec. III C);*/
+                        /* needs p_basis = 1 and at most 256 q points per axis; the handle then */
+                        /* holds max(1, max_batch) x nmodes derivative arrays of a state        */
 } chfpe_options;
 
 /* Create a handle for one model on one grid.  Validates the structs, builds the coefficient

@@ -51,7 +51,7 @@ class chfpe_grid(ctypes.Structure):
 class chfpe_options(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int), ("precision", ctypes.c_int), ("dt", ctypes.c_double),
                 ("max_batch", ctypes.c_int), ("stream", ctypes.c_void_p), ("bf16_tier", ctypes.c_int),
-                ("truncation", ctypes.c_int), ("p_basis", ctypes.c_int)]
+                ("truncation", ctypes.c_int), ("p_basis", ctypes.c_int), ("q_scheme", ctypes.c_int)]
 
 
 class chfpe_stats(ctypes.Structure):
@@ -253,13 +253,14 @@ class Handle:
 
     def __init__(self, model, grid, depth: int, dt: float, precision: int = 32,
                  max_batch: int = 1, stream: int | None = None, bf16_tier: int = 0,
-                 p_basis: int = 0):
-        """p_basis = 1: momenta in grid.np[s] Hermite functions (states hold coefficients)."""
+                 p_basis: int = 0, q_scheme: int = 0):
+        """p_basis = 1: momenta in grid.np[s] Hermite functions (states hold coefficients);
+        q_scheme = 1 (with p_basis = 1): compact q-derivatives solved by PCR."""
         lib = load()
         self._m, self._g = make_model(model), make_grid(grid)
         self._o = chfpe_options(depth=int(depth), precision=int(precision), dt=float(dt),
                                 max_batch=int(max_batch), stream=stream, bf16_tier=int(bf16_tier),
-                                p_basis=int(p_basis))
+                                p_basis=int(p_basis), q_scheme=int(q_scheme))
         h = _H()
         _check(lib.chfpe_create(ctypes.byref(self._m), ctypes.byref(self._g),
                                 ctypes.byref(self._o), ctypes.byref(h)))

@@ -55,6 +55,12 @@ struct chfpe_handle {
     chfpe_options opts;
     int d = 0, depth = 0, M = 0, prec = 32;
     int basis = 0;              // 0: momenta on a uniform grid; 1: Hermite functions (np = K_s)
+    int qscheme = 0;            // Hermite momenta: 0 explicit q stencils, 1 compact (Sec. III B)
+    void *dq = nullptr;         // compact scheme: [dq_batch][d][M][P] q-derivatives (handle precision)
+    int dq_batch = 0;           // states one derivative pass covers
+    void *pcr = nullptr;        // compact scheme: PCR row multipliers per q axis (handle precision)
+    long long pcr_off[3] = {0}; // element offset of axis s's table
+    int pcr_levels[3] = {0};
     int P = 0, Pp = 0, NQ = 0;
     int n[6] = {0}, st[6] = {0};
     double lo[6] = {0}, h[6] = {0};
@@ -184,7 +190,8 @@ static HStageArgs<T> hstage_args(const chfpe_handle *h) {
     const chfpe_model &m = h->model;
     for (int s = 0; s < h->d; ++s) {
         const double smkT = std::sqrt(m.m[s] * m.kT);
-        g.cq[s] = (T)(smkT / m.m[s] / (60.0 * h->h[s]));
+        // explicit: the stencil sum carries 60 h; compact: the derivative arrays are d/dq itself
+        g.cq[s] = (T)(smkT / m.m[s] / (h->qscheme ? 1.0 : 60.0 * h->h[s]));
         g.qlo[s] = (T)h->lo[s];
         g.qh[s] = (T)h->h[s];
         g.VLL[s] = (T)m.V_LL[s];
@@ -233,14 +240,48 @@ static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *
                           int batch) {
     if (h->basis) {
         HStageArgs<T> a = hstage_args<T>(h);
-        a.in = (const char *)in;
-        a.y = (const char *)y;
-        a.out = (char *)out;
         a.c = (T)c;
-        if (!launch_hstage<T>(h->d, h->depth, a, batch, h->stream))
-            return fail(CHFPE_EINVAL, "unsupported (d, depth)");
-        CK(cudaGetLastError());
-        ++h->launches;
+        if (!h->qscheme) {
+            a.in = (const char *)in;
+            a.y = (const char *)y;
+            a.out = (char *)out;
+            if (!launch_hstage<T>(h->d, h->depth, a, batch, h->stream))
+                return fail(CHFPE_EINVAL, "unsupported (d, depth)");
+            CK(cudaGetLastError());
+            ++h->launches;
+            return CHFPE_OK;
+        }
+        // compact q-derivatives: per chunk of dq_batch states, one PCR pass per q axis into the
+        // derivative arrays, then the stage kernel reading them
+        const long long sbytes = a.state_bytes;
+        a.dq = (const T *)h->dq;
+        a.dq_state = h->state;
+        for (int b0 = 0; b0 < batch; b0 += h->dq_batch) {
+            const int nb = std::min(h->dq_batch, batch - b0);
+            const long long off = (long long)b0 * sbytes;
+            for (int s = 0; s < h->d; ++s) {
+                HDerivArgs<T> da;
+                da.in = (const char *)in + off;
+                da.in_state = sbytes;
+                da.out = (T *)h->dq + (long long)s * h->state;
+                da.out_state = (long long)h->d * h->state;
+                da.n = h->n[s];
+                da.st = h->st[s];
+                da.lines = (int)(h->state / h->n[s]);
+                da.levels = h->pcr_levels[s];
+                da.coef = (const T *)h->pcr + h->pcr_off[s];
+                launch_hderiv<T>(da, nb, h->stream);
+                CK(cudaGetLastError());
+                ++h->launches;
+            }
+            a.in = (const char *)in + off;
+            a.y = y ? (const char *)y + off : nullptr;
+            a.out = (char *)out + off;
+            if (!launch_hstage<T>(h->d, h->depth, a, nb, h->stream))
+                return fail(CHFPE_EINVAL, "unsupported (d, depth)");
+            CK(cudaGetLastError());
+            ++h->launches;
+        }
         return CHFPE_OK;
     }
     StageArgs<T> a = stage_args<T>(h);
@@ -586,7 +627,9 @@ static double spectral_bound(const chfpe_handle *h) {
     if (h->basis) {
         // Hermite momenta: per mode the ladder block (entries sqrt(k) D+-, a tridiagonal in k) is
         // bounded by 2 sqrt(K-1) max|D+-|, |D+-| <= max|dU/dq|/(2 sqrt(mkT)) + sqrt(mkT)/m K/h_q;
-        // the links by 2 sqrt(depth c) max|V'| sqrt(K) / sqrt(mkT)
+        // the links by 2 sqrt(depth c) max|V'| sqrt(K) / sqrt(mkT).  The compact scheme's
+        // modified wavenumber (2a sin t + 2b sin 2t) / (1 + 2 alpha cos t) stays below 1.99.
+        const double K = h->qscheme ? 1.99 : 1.59;
         for (int s = 0; s < h->d; ++s) {
             const double hq = h->h[s], Kh = h->n[h->d + s], smkT = std::sqrt(m.m[s] * m.kT);
             const double qmax = std::fmax(std::fabs(h->lo[s]), std::fabs(h->lo[s] + (h->n[s] - 1) * hq));
@@ -636,6 +679,13 @@ static chfpe_status validate(const chfpe_model *m, const chfpe_grid *g, const ch
     if (o->p_basis != 0 && o->p_basis != 1) return fail(CHFPE_EINVAL, "p_basis must be 0 (grid) or 1 (Hermite)");
     if (o->p_basis == 1 && o->bf16_tier > 0)
         return fail(CHFPE_EINVAL, "bf16 tiers are built for grid momenta only");
+    if (o->q_scheme != 0 && o->q_scheme != 1)
+        return fail(CHFPE_EINVAL, "q_scheme must be 0 (explicit) or 1 (compact)");
+    if (o->q_scheme == 1) {
+        if (o->p_basis != 1) return fail(CHFPE_EINVAL, "the compact q scheme is built for Hermite momenta (p_basis 1)");
+        for (int s = 0; s < m->nmodes; ++s)
+            if (g->nq[s] > 256) return fail(CHFPE_EINVAL, "the compact q scheme takes at most 256 q points per axis");
+    }
     if (!(o->dt > 0) || !is_fin(o->dt)) return fail(CHFPE_EINVAL, "dt must be positive");
     if (o->max_batch < 0 || o->max_batch > 65535) return fail(CHFPE_EINVAL, "max_batch must be in 0..65535");
     long long P = 1;
@@ -667,7 +717,7 @@ extern "C" void chfpe_destroy(chfpe_handle *h) {
     if (h->borrowed_arenas) h->cy = h->ca = h->cb = h->eq = nullptr;
     void *ptrs[] = {h->U_d, h->F_d, h->F_f, h->wp, h->CWq, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
                     h->cy, h->ca, h->cb, h->by, h->ba, h->bb, h->eq, h->stage64, h->partial, h->dR,
-                    h->counter, h->d_err, h->d_bar, h->d_geo};
+                    h->counter, h->d_err, h->d_bar, h->d_geo, h->dq, h->pcr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->lv_ptr.empty()) {            // work lists still owned by d_work (set-up failed)
@@ -700,6 +750,7 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
     h->esize = h->prec == 64 ? 8 : 4;
     h->dt = opts->dt;
     h->basis = opts->p_basis;
+    h->qscheme = opts->q_scheme;
     const int d = h->d;
     for (int s = 0; s < d; ++s) {
         h->n[s] = grid->nq[s];
@@ -787,6 +838,59 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
     void **barenas[] = {&h->by, &h->ba, &h->bb};
     for (void **p : barenas)
         if (!st && opts->max_batch > 0) *p = (void *)dalloc<char>(sbytes * opts->max_batch, &st);
+    if (!st && h->qscheme) {
+        h->dq_batch = std::max(1, opts->max_batch);
+        h->dq = (void *)dalloc<char>((size_t)h->dq_batch * d * h->state * h->esize, &st);
+        // PCR tables (Sec. III C) of A = tridiag(1/3, 1, 1/3) per q axis, in FP64, then stored in
+        // the handle precision: [levels][2][n] multipliers, [n] 1 / (b_i h)
+        std::vector<double> tab;
+        for (int s = 0; s < d && !st; ++s) {
+            const int n = h->n[s];
+            int L = 0;
+            while ((1 << L) < n) ++L;
+            h->pcr_levels[s] = L;
+            h->pcr_off[s] = (long long)tab.size();
+            std::vector<double> lo(n), di(n, 1.0), up(n), nlo(n), ndi(n), nup(n);
+            for (int i = 0; i < n; ++i) {
+                lo[i] = i >= 1 ? 1.0 / 3.0 : 0.0;
+                up[i] = i + 1 < n ? 1.0 / 3.0 : 0.0;
+            }
+            for (int l = 0; l < L; ++l) {
+                const int o = 1 << l;
+                std::vector<double> k1(n, 0.0), k2(n, 0.0);
+                for (int i = 0; i < n; ++i) {
+                    if (i - o >= 0) k1[i] = lo[i] / di[i - o];
+                    if (i + o < n) k2[i] = up[i] / di[i + o];
+                    nlo[i] = i - o >= 0 ? -lo[i - o] * k1[i] : 0.0;
+                    nup[i] = i + o < n ? -up[i + o] * k2[i] : 0.0;
+                    ndi[i] = di[i] - (i - o >= 0 ? up[i - o] * k1[i] : 0.0) -
+                             (i + o < n ? lo[i + o] * k2[i] : 0.0);
+                }
+                lo.swap(nlo);
+                di.swap(ndi);
+                up.swap(nup);
+                tab.insert(tab.end(), k1.begin(), k1.end());
+                tab.insert(tab.end(), k2.begin(), k2.end());
+            }
+            for (int i = 0; i < n; ++i) tab.push_back(1.0 / (di[i] * h->h[s]));
+            const cudaError_t ce = h->prec == 64 ? configure_hderiv<double>(n) : configure_hderiv<float>(n);
+            if (ce != cudaSuccess) st = fail(CHFPE_ECUDA, std::string("PCR shared memory: ") + cudaGetErrorString(ce));
+        }
+        if (!st) {
+            if (h->prec == 64) {
+                double *t = dalloc<double>(tab.size(), &st);
+                if (!st && cudaMemcpy(t, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+                    st = fail(CHFPE_ECUDA, "PCR table upload");
+                h->pcr = t;
+            } else {
+                std::vector<float> tf(tab.begin(), tab.end());
+                float *t = dalloc<float>(tf.size(), &st);
+                if (!st && cudaMemcpy(t, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                    st = fail(CHFPE_ECUDA, "PCR table upload");
+                h->pcr = t;
+            }
+        }
+    }
     if (st) { chfpe_destroy(h); return st; }
 
     // coefficient tables

@@ -9,7 +9,37 @@ constexpr int kHNT = 128;
 
 template <typename T, int D, int K>
 void launch_one(const HStageArgs<T> &a, int batch, cudaStream_t s) {
-    hstage_kernel<T, D, K, kHNT><<<dim3((a.g.P + kHNT - 1) / kHNT, batch), kHNT, 0, s>>>(a);
+    const dim3 grid((a.g.P + kHNT - 1) / kHNT, batch);
+    if (a.dq)
+        hstage_kernel<T, D, K, kHNT, true><<<grid, kHNT, 0, s>>>(a);
+    else
+        hstage_kernel<T, D, K, kHNT><<<grid, kHNT, 0, s>>>(a);
+}
+
+template <typename T>
+size_t deriv_smem(int n) { return (size_t)2 * n * kPcrCols * sizeof(T); }
+
+// largest dynamic shared memory opted into so far, per element type
+template <typename T>
+size_t &deriv_configured() {
+    static size_t c = 48 * 1024;
+    return c;
+}
+
+template <typename T>
+cudaError_t configure_deriv(int n) {
+    const size_t smem = deriv_smem<T>(n);
+    if (smem <= deriv_configured<T>()) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(hderiv_pcr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess) deriv_configured<T>() = smem;
+    return e;
+}
+
+template <typename T>
+void launch_deriv(const HDerivArgs<T> &a, int batch, cudaStream_t s) {
+    hderiv_pcr_kernel<T><<<dim3((a.lines + kPcrCols - 1) / kPcrCols, batch), dim3(kPcrCols, kPcrRows),
+                           deriv_smem<T>(a.n), s>>>(a);
 }
 
 template <typename T>
@@ -34,6 +64,22 @@ bool launch_hstage<float>(int d, int depth, const HStageArgs<float> &a, int batc
 template <>
 bool launch_hstage<double>(int d, int depth, const HStageArgs<double> &a, int batch, cudaStream_t s) {
     return launch_any<double>(d, depth, a, batch, s);
+}
+
+template <>
+cudaError_t configure_hderiv<float>(int n) { return configure_deriv<float>(n); }
+
+template <>
+cudaError_t configure_hderiv<double>(int n) { return configure_deriv<double>(n); }
+
+template <>
+void launch_hderiv<float>(const HDerivArgs<float> &a, int batch, cudaStream_t s) {
+    launch_deriv<float>(a, batch, s);
+}
+
+template <>
+void launch_hderiv<double>(const HDerivArgs<double> &a, int batch, cudaStream_t s) {
+    launch_deriv<double>(a, batch, s);
 }
 
 }  // namespace chfpe

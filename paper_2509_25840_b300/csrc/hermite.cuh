@@ -10,9 +10,20 @@
 //               + sum_s sqrt(n_s c_s)     V_s' sqrt(k_s+1) / sqrt(m_s kT) c^(n-e_s)_{k+e_s}
 //   D+-_s = dU/dq_s / (2 sqrt(m_s kT)) -+ (sqrt(m_s kT) / m_s) d/dq_s
 // (c_s = zeta_s gamma_s m_s kT; coefficients with k_s outside [0, K_s) are zero; d/dq_s the
-// 6th-order central difference with zero values outside the q-grid).  The insertion X^x raises
-// k:  (X^x c)_k = -sum_s dX/dq_s sqrt(k_s) / sqrt(m_s kT) c_{k-e_s};  only c^(0)_0 reaches the
-// observable.
+// 6th-order central difference with zero values outside the q-grid, or the compact scheme of
+// Sec. III B).  The insertion X^x raises k:  (X^x c)_k = -sum_s dX/dq_s sqrt(k_s) / sqrt(m_s kT)
+// c_{k-e_s};  only c^(0)_0 reaches the observable.
+//
+// Compact q-derivatives (Sec. III B, Eqs. for A_i and B_i): along every q line,
+//   A f' = B f / h,  A = tridiag(1/3, 1, 1/3),  (B f)_i = a (f_{i+1} - f_{i-1}) + b (f_{i+2} - f_{i-2}),
+// zero values outside the line, a = 7/9, b = 1/36 (the sixth-order Pade scheme; the printed
+// a = 7/18 is inconsistent with alpha = 1/3 and is read as 7/9).  hderiv_pcr_kernel forms B f and
+// solves the tridiagonal systems of a tile of lines by parallel cyclic reduction (Sec. III C) in
+// shared memory: ceil(log2 n) levels, at level l every row i eliminates its couplings to rows
+// i -+ 2^l with those rows' equations, after which every row stands alone.  A is the same for
+// every line, so the row multipliers of every level (and the final 1/(b_i h)) are computed once
+// on the host in FP64; the device updates only the right-hand sides.  The stage kernel then
+// reads the derivative arrays instead of forming stencils.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,8 +51,69 @@ struct HStageArgs {
     char *out;
     long long state_bytes;
     T c;
+    const T *dq;                // compact scheme: d/dq_s of state b at dq + (b D + s) dq_state
+    long long dq_state;         // (elements; nullptr: explicit stencils, cq holds 1/(60 h) then)
     HGeo<T> g;
 };
+
+// Tile of 32 q lines along one axis: every line is n values `st` elements apart; line l of a
+// state starts at (l / st) n st + l % st (the member index is the outermost part of l / st)
+template <typename T>
+struct HDerivArgs {
+    const char *in;             // batch of states, in_state bytes apart
+    long long in_state;
+    T *out;                     // derivatives: out + b out_state + (same offset as the input)
+    long long out_state;        // elements
+    int n, st, lines;           // line length, axis stride, lines per state (M P / n)
+    int levels;                 // PCR levels, 2^levels >= n
+    const T *coef;              // [levels][2][n] row multipliers (rows i - 2^l, i + 2^l), then
+                                // [n] 1 / (b_i h) of the reduced diagonal
+};
+
+constexpr int kPcrCols = 32, kPcrRows = 8;
+
+// compact first derivative along one q axis of a tile of 32 lines of every state in the batch
+// (blockIdx.y): load, B f, PCR, scale, store; 2 n 32 values of shared memory
+template <typename T>
+__global__ void __launch_bounds__(kPcrCols * kPcrRows) hderiv_pcr_kernel(const HDerivArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char pcr_smem[];
+    T *cur = reinterpret_cast<T *>(pcr_smem);
+    T *nxt = cur + a.n * kPcrCols;
+    const int tx = threadIdx.x, ty = threadIdx.y, n = a.n;
+    const int line = blockIdx.x * kPcrCols + tx;
+    const bool ok = line < a.lines;
+    const int outer = ok ? line / a.st : 0;
+    const long long base = (long long)outer * n * a.st + (ok ? line - outer * a.st : 0);
+    const T *f = reinterpret_cast<const T *>(a.in + (long long)blockIdx.y * a.in_state) + base;
+    for (int i = ty; i < n; i += kPcrRows) nxt[i * kPcrCols + tx] = ok ? __ldg(f + (long long)i * a.st) : T(0);
+    __syncthreads();
+    const T ca = T(7) / T(9), cb = T(1) / T(36);
+    for (int i = ty; i < n; i += kPcrRows) {
+        const T f1 = (i + 1 < n ? nxt[(i + 1) * kPcrCols + tx] : T(0)) - (i >= 1 ? nxt[(i - 1) * kPcrCols + tx] : T(0));
+        const T f2 = (i + 2 < n ? nxt[(i + 2) * kPcrCols + tx] : T(0)) - (i >= 2 ? nxt[(i - 2) * kPcrCols + tx] : T(0));
+        cur[i * kPcrCols + tx] = ca * f1 + cb * f2;
+    }
+    __syncthreads();
+    for (int l = 0; l < a.levels; ++l) {
+        const int o = 1 << l;
+        const T *k1 = a.coef + (long long)2 * l * n, *k2 = k1 + n;
+        for (int i = ty; i < n; i += kPcrRows) {
+            T v = cur[i * kPcrCols + tx];
+            if (i - o >= 0) v -= k1[i] * cur[(i - o) * kPcrCols + tx];
+            if (i + o < n) v -= k2[i] * cur[(i + o) * kPcrCols + tx];
+            nxt[i * kPcrCols + tx] = v;
+        }
+        __syncthreads();
+        T *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    const T *binv = a.coef + (long long)2 * a.levels * n;
+    if (ok) {
+        T *o = a.out + (long long)blockIdx.y * a.out_state + base;
+        for (int i = ty; i < n; i += kPcrRows) o[(long long)i * a.st] = cur[i * kPcrCols + tx] * binv[i];
+    }
+}
 
 // 45 (f+1 - f-1) - 9 (f+2 - f-2) + (f+3 - f-3) along q axis `s` of the point x (q index i)
 template <typename T>
@@ -57,7 +129,7 @@ __device__ __forceinline__ T hstencil(const T *__restrict__ f, int x, int i, int
 
 // one RK4 stage, one thread per (q, k) point for every member (gather form: each output reads the
 // q-stencils of its k +- e_s neighbours and the link values of its member neighbours)
-template <typename T, int D, int DEPTH, int NT>
+template <typename T, int D, int DEPTH, int NT, bool PRE = false>
 __global__ void __launch_bounds__(NT) hstage_kernel(const HStageArgs<T> a) {
     constexpr MemberTable<D, DEPTH> tab{};
     constexpr int M = MemberTable<D, DEPTH>::M;
@@ -68,6 +140,7 @@ __global__ void __launch_bounds__(NT) hstage_kernel(const HStageArgs<T> a) {
     const T *in = reinterpret_cast<const T *>(a.in + boff);
     T *out = reinterpret_cast<T *>(a.out + boff);
     const T *y = a.y ? reinterpret_cast<const T *>(a.y + boff) : nullptr;
+    const T *dqb = PRE ? a.dq + (long long)blockIdx.y * D * a.dq_state : nullptr;
 
     int idx[2 * D];
     {
@@ -104,12 +177,14 @@ __global__ void __launch_bounds__(NT) hstage_kernel(const HStageArgs<T> a) {
             const int sk_st = g.st[D + s];
             if (hp[s]) {             // sqrt(k+1) D+ c_{k+e_s}
                 const int xp = x + sk_st;
-                const T dq = hstencil<T>(c, xp, idx[s], g.n[s], g.st[s]);
+                const T dq = PRE ? __ldg(dqb + s * a.dq_state + (long long)m * g.P + xp)
+                                 : hstencil<T>(c, xp, idx[s], g.n[s], g.st[s]);
                 acc += sk1[s] * (F[s] * __ldg(c + xp) - g.cq[s] * dq);
             }
             if (hm[s]) {             // - sqrt(k) D- c_{k-e_s}
                 const int xm = x - sk_st;
-                const T dq = hstencil<T>(c, xm, idx[s], g.n[s], g.st[s]);
+                const T dq = PRE ? __ldg(dqb + s * a.dq_state + (long long)m * g.P + xm)
+                                 : hstencil<T>(c, xm, idx[s], g.n[s], g.st[s]);
                 acc -= sk[s] * (F[s] * __ldg(c + xm) + g.cq[s] * dq);
             }
             if (tab.up[m][s] >= 0 && hm[s]) {
@@ -194,5 +269,21 @@ template <>
 bool launch_hstage<float>(int d, int depth, const HStageArgs<float> &a, int batch, cudaStream_t s);
 template <>
 bool launch_hstage<double>(int d, int depth, const HStageArgs<double> &a, int batch, cudaStream_t s);
+
+// compact derivative along one q axis of `batch` states (hderiv_pcr_kernel); configure_hderiv
+// opts the kernel into the shared memory lines of n points need (once, before any launch or
+// stream capture that uses them)
+template <typename T>
+cudaError_t configure_hderiv(int n);
+template <>
+cudaError_t configure_hderiv<float>(int n);
+template <>
+cudaError_t configure_hderiv<double>(int n);
+template <typename T>
+void launch_hderiv(const HDerivArgs<T> &a, int batch, cudaStream_t s);
+template <>
+void launch_hderiv<float>(const HDerivArgs<float> &a, int batch, cudaStream_t s);
+template <>
+void launch_hderiv<double>(const HDerivArgs<double> &a, int batch, cudaStream_t s);
 
 }  // namespace chfpe
