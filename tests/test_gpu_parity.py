@@ -292,6 +292,26 @@ def test_every_stage_launch_shape_matches_oracle(d, n, depth, variant, monkeypat
     assert np.abs(got - want).max() <= 3e-6 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("variant", [3, 15, 16])
+def test_bench_launch_shapes_match_oracle_at_full_size(variant, monkeypatch):
+    """The launch shapes the autotuner picks on the benchmark workload, on that workload itself:
+    its model, its 32^4 grid and domain, depth 4 (15 members), FP32, against the oracle's RHS of
+    the same seeded state (every boundary case of every axis)."""
+    monkeypatch.setenv("CHFPE_STAGE_VARIANT", str(variant))
+    chfpe = _chfpe()
+    wl = inputs.two_mode_32(nt=2)
+    pb = oracle.Problem(wl.model, wl.grid, wl.depth)
+    W = _rounded(inputs.random_state(wl.grid, pb.M, seed=77, smooth=False), 32)
+    want = oracle.rhs(pb, W)
+    with chfpe.Handle(wl.model, wl.grid, depth=wl.depth, dt=wl.dt, precision=32) as h:
+        assert h.stage_tuning()[0] == variant
+        x = torch.tensor(W, dtype=torch.float32, device="cuda")
+        y = torch.empty_like(x)
+        h.rhs_device(x.data_ptr(), y.data_ptr(), 1)
+        got = y.double().cpu().numpy()
+    assert np.abs(got - want).max() <= 3e-6 * np.abs(want).max()
+
+
 def test_autotuner_times_the_shapes_and_keeps_the_fastest(monkeypatch):
     monkeypatch.delenv("CHFPE_STAGE_VARIANT", raising=False)
     model = _model(2)
