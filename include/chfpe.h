@@ -332,7 +332,10 @@ chfpe_status chfpe_surrogate_train(chfpe_surrogate *s, const float *X, const flo
                                    double *epoch_loss);
 /* The GEMM kernel alone (for tests): C[m][n] = sum_k A(m,k) B(n,k) (+ bias[n]) with BF16 A, B
  * and FP32 C, A(m,k) = ta ? A[k*lda + m] : A[m*lda + k], B(n,k) = tb ? B[k*ldb + n] : B[n*ldb + k],
- * C row-major [M][N].  splits > 1 splits K and ADDS into C; splits == 1 overwrites C. */
+ * C row-major [M][N].  splits > 1 splits K and ADDS into C; splits == 1 overwrites C.  Runs on the
+ * tcgen05 tensor cores (128 x 128 output tiles, FP32 accumulation in tensor memory); with
+ * CHFPE_SURROGATE_GEMM=mma in the environment on the warp-level mma.sync kernel instead.
+ * Synchronous (it reads the error word of the kernel's bounded waits: CHFPE_ETIMEOUT). */
 chfpe_status chfpe_surrogate_gemm(const void *A, int ta, int lda, const void *B, int tb, int ldb,
                                   float *C, const float *bias, int M, int N, int K, int splits,
                                   void *stream);

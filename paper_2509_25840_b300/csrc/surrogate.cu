@@ -10,17 +10,21 @@
 // Loss: mean over pixels of (y - t)^2 + w_s * mean over the batch of (s - t_s)^2.
 //
 // Every contraction -- the linear layers, the convolutions as im2col GEMMs, their data gradients
-// and their weight gradients -- runs in one hand-written kernel: BF16 tensor-core
-// mma.sync.m16n8k16 with FP32 accumulation, operands read in either storage order so that no
-// transposed copy is ever made.  Training keeps FP32 master weights, FP32 gradients and FP32
+// and their weight gradients -- runs in one hand-written kernel: BF16 on the tcgen05 tensor cores
+// with FP32 accumulation in tensor memory (tc_gemm.cuh), operands read in either storage order so
+// that no transposed copy is ever made.  The earlier warp-level mma.sync.m16n8k16 kernel stays
+// selectable (CHFPE_SURROGATE_GEMM=mma) for comparison.  Training keeps FP32 master weights, FP32 gradients and FP32
 // AdamW moments; the BF16 weight copy the GEMMs read is refreshed after every update.
 #include "../../include/chfpe.h"
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "tc_gemm.cuh"
+
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -430,6 +434,55 @@ chfpe_status dalloc(chfpe_surrogate *h, T **ptr, long long n) {
     return CHFPE_OK;
 }
 
+// error word of the tensor-core GEMM's bounded waits (set on the device, read after a stream
+// synchronisation by tc_check)
+__device__ int g_tc_err;
+
+int *tc_err_ptr() {
+    static int *p = nullptr;
+    if (!p && cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_tc_err) != cudaSuccess) p = nullptr;
+    return p;
+}
+
+// the tcgen05 kernels need more than 48 KB of dynamic shared memory: opt in once per instantiation
+cudaError_t tc_configure() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(chfpe::tc::gemm_tc_kernel<false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, chfpe::tc::kSmemBytes);
+    if (!e) e = cudaFuncSetAttribute(chfpe::tc::gemm_tc_kernel<false, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, chfpe::tc::kSmemBytes);
+    if (!e) e = cudaFuncSetAttribute(chfpe::tc::gemm_tc_kernel<true, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, chfpe::tc::kSmemBytes);
+    if (!e) e = cudaFuncSetAttribute(chfpe::tc::gemm_tc_kernel<true, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, chfpe::tc::kSmemBytes);
+    if (!e) e = tc_err_ptr() ? cudaSuccess : cudaErrorInvalidSymbol;
+    if (!e) e = cudaMemset(tc_err_ptr(), 0, sizeof(int));
+    done = e == cudaSuccess;
+    return e;
+}
+
+// after a synchronisation of the stream: CHFPE_ETIMEOUT if a tensor-core GEMM's wait ran out
+chfpe_status tc_check(cudaStream_t s) {
+    int *p = tc_err_ptr();
+    if (!p) return CHFPE_OK;
+    int v = 0;
+    SCK(cudaMemcpyAsync(&v, p, sizeof v, cudaMemcpyDeviceToHost, s));
+    SCK(cudaStreamSynchronize(s));
+    if (v) {
+        SCK(cudaMemsetAsync(p, 0, sizeof(int), s));
+        return sfail(CHFPE_ETIMEOUT, "surrogate: a tensor-core GEMM wait timed out");
+    }
+    return CHFPE_OK;
+}
+
+// CHFPE_SURROGATE_GEMM=mma selects the mma.sync kernel (kept for comparison); the default is the
+// tcgen05 kernel
+bool use_tc() {
+    const char *e = getenv("CHFPE_SURROGATE_GEMM");
+    return !(e && e[0] == 'm');
+}
+
 template <bool TA, bool TB>
 chfpe_status gemm_t(cudaStream_t s, const bf16 *A, int lda, const bf16 *B, int ldb, float *C,
                     const float *bias, int M, int N, int K, int splits) {
@@ -437,6 +490,20 @@ chfpe_status gemm_t(cudaStream_t s, const bf16 *A, int lda, const bf16 *B, int l
     if (M <= 0 || N <= 0) return CHFPE_OK;
     if (K <= 0) {
         if (!accumulate) SCK(cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), s));
+        return CHFPE_OK;
+    }
+    if (use_tc() && (M + chfpe::tc::kBM - 1) / chfpe::tc::kBM <= 65535) {
+        using namespace chfpe::tc;
+        SCK(tc_configure());
+        splits = std::max(1, std::min(splits, (K + kBK - 1) / kBK));
+        int klen = (K + splits - 1) / splits;
+        klen = (klen + kBK - 1) / kBK * kBK;
+        const int nz = (K + klen - 1) / klen;
+        const int BN = N >= 128 ? 128 : (N + 15) / 16 * 16;
+        dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM, nz);
+        gemm_tc_kernel<TA, TB><<<grid, kThreads, kSmemBytes, s>>>(A, lda, B, ldb, C, bias, M, N, K,
+                                                                  klen, accumulate, BN, tc_err_ptr());
+        SLAUNCH();
         return CHFPE_OK;
     }
     splits = std::max(1, std::min(splits, (K + GK - 1) / GK));
@@ -775,6 +842,7 @@ chfpe_status chfpe_surrogate_gradients(chfpe_surrogate *h, const float *X, const
         SCK(cudaMemcpyAsync(gp.data(), h->g, h->nparam * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     }
     SCK(cudaStreamSynchronize(h->stream));
+    if ((st = tc_check(h->stream))) return st;
     if (grad_host) repack(h, gp.data(), grad_host, false);
     return CHFPE_OK;
 }
@@ -823,7 +891,7 @@ chfpe_status chfpe_surrogate_train(chfpe_surrogate *h, const float *X, const flo
     cudaFree(dperm);
     if (st != CHFPE_OK) return st;
     if (e != cudaSuccess) return sfail(CHFPE_ECUDA, std::string("surrogate_train: ") + cudaGetErrorString(e));
-    return CHFPE_OK;
+    return tc_check(h->stream);
 }
 
 chfpe_status chfpe_surrogate_gemm(const void *A, int ta, int lda, const void *B, int tb, int ldb,
@@ -831,8 +899,10 @@ chfpe_status chfpe_surrogate_gemm(const void *A, int ta, int lda, const void *B,
                                   void *stream) {
     if (!A || !B || !C || M < 0 || N < 0 || K < 0 || splits < 1 || lda < 1 || ldb < 1)
         return sfail(CHFPE_EINVAL, "surrogate_gemm: bad arguments");
-    return gemm(static_cast<cudaStream_t>(stream), ta != 0, static_cast<const bf16 *>(A), lda,
-                tb != 0, static_cast<const bf16 *>(B), ldb, C, bias, M, N, K, splits);
+    const chfpe_status st = gemm(static_cast<cudaStream_t>(stream), ta != 0, static_cast<const bf16 *>(A),
+                                 lda, tb != 0, static_cast<const bf16 *>(B), ldb, C, bias, M, N, K, splits);
+    if (st) return st;
+    return tc_check(static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -40,10 +40,18 @@ def _chfpe():
     return chfpe
 
 
+@pytest.mark.parametrize("path", ["tcgen05", "mma"])
 @pytest.mark.parametrize("ta,tb", [(False, False), (False, True), (True, False), (True, True)])
 @pytest.mark.parametrize("M,N,K,splits", [(1, 1, 1, 1), (70, 45, 33, 1), (130, 64, 300, 3),
-                                          (64, 200, 16, 1), (5, 80, 4099, 7)])
-def test_gemm_bf16_matches_exact_products(ta, tb, M, N, K, splits):
+                                          (64, 200, 16, 1), (5, 80, 4099, 7), (300, 200, 520, 3),
+                                          (256, 512, 512, 1), (1000, 8, 288, 1)])
+def test_gemm_bf16_matches_exact_products(ta, tb, M, N, K, splits, path, monkeypatch):
+    """Both GEMM kernels (tcgen05 with TMEM accumulators, the default; warp-level mma.sync),
+    every storage order, ragged tiles in M, N and K, split-K, and the surrogate's own shapes."""
+    if path == "mma":
+        monkeypatch.setenv("CHFPE_SURROGATE_GEMM", "mma")
+    else:
+        monkeypatch.delenv("CHFPE_SURROGATE_GEMM", raising=False)
     chfpe = _chfpe()
     rng = np.random.default_rng(M * 1000 + N * 10 + K)
     A = so.bf16_round(rng.standard_normal((M, K)))
