@@ -499,7 +499,9 @@ chfpe_status gemm_t(cudaStream_t s, const bf16 *A, int lda, const bf16 *B, int l
         int klen = (K + splits - 1) / splits;
         klen = (klen + kBK - 1) / kBK * kBK;
         const int nz = (K + klen - 1) / klen;
-        const int BN = N >= 128 ? 128 : (N + 15) / 16 * 16;
+        // 128-wide tiles when they fill the GPU twice over, else at most 64 (more CTAs)
+        const long long t128 = (long long)((N + 127) / 128) * ((M + kBM - 1) / kBM) * nz;
+        const int BN = (N >= 128 && t128 >= 2 * 148) ? 128 : std::min(64, (N + 15) / 16 * 16);
         dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM, nz);
         gemm_tc_kernel<TA, TB><<<grid, kThreads, kSmemBytes, s>>>(A, lda, B, ldb, C, bias, M, N, K,
                                                                   klen, accumulate, BN, tc_err_ptr());

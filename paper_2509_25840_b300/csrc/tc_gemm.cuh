@@ -4,21 +4,25 @@
 //   C[m][n] (=, or += with FP32 atomics under split-K) sum_k A(m, k) B(n, k)  (+ bias[n])
 //   A(m, k) = TA ? A[k * lda + m] : A[m * lda + k];   B(n, k) = TB ? B[k * ldb + n] : B[n * ldb + k]
 //
-// One CTA of 128 threads computes a 128 x BN tile of C.  K is walked in tiles of 64: all threads
-// copy the A and B tiles from global memory into shared memory (two buffers), laid out as the
-// tensor core's canonical K-major arrangement without swizzling -- 8 x 8 "core matrices" of 128
-// contiguous bytes (8 rows of 8 BF16 along k), the core matrices of one 8-row group rows / 8 *
-// 128 B apart along k (the leading-dimension offset) and consecutive 8-row groups 128 B apart
-// (the stride offset).  Either storage order of either operand is transposed during that copy, so the MMA
-// only ever reads K-major tiles.  One elected thread then issues four tcgen05.mma (M = 128,
-// N = BN, K = 16, BF16 x BF16 -> FP32) that accumulate into tensor memory (TMEM: 128 lanes = rows,
-// BN columns), and tcgen05.commit arrives on the buffer's mbarrier once they have completed, which
-// tells the copy two tiles later that the buffer is free.  The epilogue waits for the last
-// commit, and each warp reads its 32 rows of the accumulator from TMEM (tcgen05.ld, 16 columns at
-// a time), adds the bias and stores (or atomically adds) FP32 results.
+// One CTA of 128 threads computes a 128 x BN tile of C (BN a multiple of 16 up to 128).  K is
+// walked in tiles of 32 through a ring of kStages shared-memory buffers.  Each tile is laid out as
+// the tensor core's canonical K-major arrangement without swizzling: 8 x 8 "core matrices" of 128
+// contiguous bytes (8 rows of 8 BF16 along k); the core matrices of one 8-row group lie rows / 8 *
+// 128 B apart along k (the descriptor's leading-dimension offset) and consecutive 8-row groups
+// 128 B apart (its stride offset).  Operands stored row by row (k contiguous) are copied with
+// 16-byte cp.async (zero-filled outside the matrix), kStages - 1 tiles ahead of the MMAs, into
+// K-major core matrices; operands stored k-major go the same way into MN-major core matrices,
+// which the MMA reads transposed (the operand's major bit of the instruction descriptor), so no
+// operand is ever transposed by the threads.  One thread issues two
+// tcgen05.mma (M = 128, N = BN, K = 16, BF16 x BF16 -> FP32) per tile, accumulating in tensor
+// memory (TMEM: 128 lanes = rows, BN columns), and tcgen05.commit arrives on the tile's buffer
+// mbarrier once they have completed, which frees the buffer for the copy kStages - 1 tiles later.
+// The epilogue waits for the last commit; each warp reads its 32 rows of the accumulator from
+// TMEM (tcgen05.ld, 16 columns at a time), adds the bias and stores (or atomically adds) FP32.
 //
-// Every wait on an mbarrier is bounded; a wait that runs out sets *err (the caller turns it into
-// an error status), and the CTA still waits (bounded) for its own MMAs before it frees TMEM.
+// Every wait on an mbarrier is bounded and decided for the whole block; a wait that runs out sets
+// *err (the caller turns it into an error status), and the CTA still waits (bounded) for its own
+// MMAs before it frees TMEM.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -32,8 +36,16 @@ namespace tc {
 typedef __nv_bfloat16 bf16;
 
 constexpr int kBM = 128;            // rows of a C tile (TMEM lanes)
-constexpr int kBK = 64;             // k per shared-memory tile (four MMAs of K = 16)
+constexpr int kBK = 32;             // k per shared-memory tile (two MMAs of K = 16)
+constexpr int kStages = 4;          // shared-memory tiles in flight
 constexpr int kThreads = 128;
+constexpr int kTileA = kBM * kBK * 2, kTileB = 128 * kBK * 2;   // bytes (B tile for BN = 128)
+constexpr int kStageBytes = kTileA + kTileB;
+constexpr int kSmemTiles = kStages * kStageBytes;
+constexpr int kSmemBytes = kSmemTiles + 128;                       // + mbarriers, TMEM address
+// TMEM columns a CTA allocates (FP32 accumulator columns, BN <= 128); three CTAs per SM (3 x 64 KB
+// of shared memory) hold 384 of the SM's 512
+constexpr int kTmemCols = 128;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -52,9 +64,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A (bits 7-9 = 1) and
-// B (bits 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28
-__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// B (bits 10-12 = 1), A MN-major if ta (bit 15), B MN-major if tb (bit 16), N >> 3 in bits 17-22,
+// M >> 4 in bits 24-28
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, bool ta, bool tb) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((ta ? 1u : 0u) << 15) | ((tb ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
@@ -78,68 +92,65 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
     return false;
 }
 
-// tile rows r0.. of operand X into the canonical K-major layout of shared memory:
-// core matrix (row group g, k group j) at byte (j * rows / 8 + g) * 128, row r % 8 at +16 (r % 8)
-// T = true: X is stored k-major in global memory (element (r, k) at X[k * ld + r])
+// 16 bytes global -> shared, asynchronous; src_bytes = 0 writes zeros and reads nothing
+__device__ __forceinline__ void cp16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+// tile rows r0.. (rows_tile of them) of operand X, k in [k0, k0 + 32), into shared memory: core
+// matrix (row group g, k group j) at byte (j * rows_tile / 8 + g) * 128 (so the descriptor's
+// leading-dimension offset, along k, is rows_tile / 8 * 128 B and its stride offset, along the
+// rows, 128 B, in both orientations); zeros outside (rows, kend).  Whole aligned 16-byte chunks go
+// by cp.async, the rest element by element.
+// T = false: X row by row (element (r, k) at X[r * ld + k]); K-major core matrices (8 rows of 8 k)
+// T = true: X k-major (element (r, k) at X[k * ld + r]); MN-major core matrices (8 k of 8 rows),
+//           which the MMA reads with the operand's transpose bit set
 template <bool T>
 __device__ __forceinline__ void load_tile(unsigned char *S, int rows_tile, const bf16 *__restrict__ X,
                                           int ld, int rows, int kend, int r0, int k0) {
     const int groups = rows_tile / 8;
     if (!T) {
-        // 16-byte chunks (row r, k group j): rows_tile * 8 chunks
-        for (int c = threadIdx.x; c < rows_tile * 8; c += kThreads) {
-            const int r = c >> 3, j = c & 7;
+        for (int c = threadIdx.x; c < rows_tile * (kBK / 8); c += kThreads) {
+            const int r = c / (kBK / 8), j = c % (kBK / 8);
             const int gr = r0 + r, gk = k0 + j * 8;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (gr < rows && gk < kend) {
-                const bf16 *src = X + (long long)gr * ld + gk;
-                if (gk + 8 <= kend && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-                    v = __ldg(reinterpret_cast<const uint4 *>(src));
-                } else {
-                    bf16 t[8];
+            unsigned char *dst = S + (j * groups + (r >> 3)) * 128 + (r & 7) * 16;
+            const bool in = gr < rows && gk < kend;
+            const bf16 *src = X + (long long)(in ? gr : 0) * ld + (in ? gk : 0);
+            if (!in || (gk + 8 <= kend && (reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+                cp16(dst, src, in ? 16 : 0);
+            } else {
+                bf16 t[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) t[e] = (gk + e < kend) ? src[e] : __float2bfloat16(0.f);
-                    memcpy(&v, t, 16);
-                }
+                for (int e = 0; e < 8; ++e) t[e] = (gk + e < kend) ? src[e] : __float2bfloat16(0.f);
+                uint4 v;
+                memcpy(&v, t, 16);
+                *reinterpret_cast<uint4 *>(dst) = v;
             }
-            *reinterpret_cast<uint4 *>(S + (j * groups + (r >> 3)) * 128 + (r & 7) * 16) = v;
         }
     } else {
-        // 16-byte chunks (k, row group g) of 8 consecutive rows at one k, scattered to 8 rows
+        // MN-major core matrices: (row group g, k group j) holds 8 k-rows of 8 consecutive
+        // matrix rows, so a 16-byte global chunk (8 rows at one k) is one core-matrix row
         for (int c = threadIdx.x; c < kBK * groups; c += kThreads) {
             const int k = c / groups, g = c - k * groups;
             const int gk = k0 + k, gr = r0 + g * 8;
-            bf16 t[8];
-            if (gk < kend && gr < rows) {
-                const bf16 *src = X + (long long)gk * ld + gr;
-                if (gr + 8 <= rows && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-                    uint4 v = __ldg(reinterpret_cast<const uint4 *>(src));
-                    memcpy(t, &v, 16);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) t[e] = (gr + e < rows) ? src[e] : __float2bfloat16(0.f);
-                }
+            unsigned char *dst = S + ((k >> 3) * groups + g) * 128 + (k & 7) * 16;
+            const bool in = gk < kend && gr < rows;
+            const bf16 *src = X + (long long)(in ? gk : 0) * ld + (in ? gr : 0);
+            if (!in || (gr + 8 <= rows && (reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+                cp16(dst, src, in ? 16 : 0);
             } else {
+                bf16 t[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) t[e] = __float2bfloat16(0.f);
+                for (int e = 0; e < 8; ++e) t[e] = (gr + e < rows) ? src[e] : __float2bfloat16(0.f);
+                uint4 v;
+                memcpy(&v, t, 16);
+                *reinterpret_cast<uint4 *>(dst) = v;
             }
-            bf16 *base = reinterpret_cast<bf16 *>(S + ((k >> 3) * groups + g) * 128) + (k & 7);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) base[e * 8] = t[e];
         }
     }
 }
-
-
-// shared memory of one CTA: two buffers of (A tile 16 KB, B tile BN x 128 B) with BN <= 128, then
-// 32 KB that no tile uses (every descriptor's reach, read either way round, stays inside the
-// allocation), then the mbarriers and the TMEM address
-constexpr int kTileA = kBM * kBK * 2, kTileB = 128 * kBK * 2;
-constexpr int kSmemTiles = 2 * (kTileA + kTileB) + 32 * 1024;
-constexpr int kSmemBytes = kSmemTiles + 64;
-// TMEM columns a CTA allocates (FP32 accumulator columns; BN <= 128 are used): twice the widest
-// tile, and two CTAs (2 x 96 KB of shared memory) per SM hold at most the SM's 512
-constexpr int kTmemCols = 256;
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
@@ -159,54 +170,52 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(
     const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, float *__restrict__ C,
-    const float *__restrict__ bias, int M, int N, int K, int klen, int accumulate, int BN,
-    int *err) {
-    constexpr int tmem_cols = kTmemCols;
+    const float *__restrict__ bias, int M, int N, int K, int klen, int accumulate, int BN, int *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kSmemTiles);      // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kSmemTiles + 16);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kSmemTiles);                 // [kStages]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kSmemTiles + 8 * kStages);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
     const int kb = blockIdx.z * klen, ke = min(K, kb + klen);
     const int nk = (ke - kb + kBK - 1) / kBK;
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_addr(tmem_slot)), "r"(tmem_cols) : "memory");
+                     ::"r"(smem_addr(tmem_slot)), "r"(kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = instr_desc(kBM, BN);   // BN a multiple of 16 in [16, 128]
+    const uint32_t idesc = instr_desc(kBM, BN, TA, TB);   // BN a multiple of 16 in [16, 128]
     const long long limit = 1ll << 24;
     bool ok = true;
     int last = -1;   // the last k tile whose MMAs were committed
 
+    auto buf = [&](int t) { return smem + (t % kStages) * kStageBytes; };
+    auto copy_tile = [&](int t) {
+        unsigned char *Sa = buf(t);
+        load_tile<TA>(Sa, kBM, A, lda, M, ke, m0, kb + t * kBK);
+        load_tile<TB>(Sa + kTileA, BN, B, ldb, N, ke, n0, kb + t * kBK);
+    };
+    // prologue: tiles 0 .. kStages - 2, one cp.async group each (empty groups keep the count)
+    for (int t = 0; t < kStages - 1; ++t) {
+        if (t < nk) copy_tile(t);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     for (int kt = 0; kt < nk; ++kt) {
-        const int b = kt & 1;
-        unsigned char *Sa = smem + b * (kTileA + kTileB);
-        unsigned char *Sb = Sa + kTileA;
-        if (kt >= 2) {   // buffer free: the MMAs of tile kt - 2 have completed (a block-wide decision)
-            if (!__syncthreads_and(mbar_wait(&bar[b], ((kt >> 1) - 1) & 1, limit) ? 1 : 0)) {
-                ok = false;
-                break;
-            }
-        }
-        const int k0 = kb + kt * kBK;
-        load_tile<TA>(Sa, kBM, A, lda, M, ke, m0, k0);
-        load_tile<TB>(Sb, BN, B, ldb, N, ke, n0, k0);
+        // tile kt is group kt: at most the kStages - 2 newest groups may still be in flight
+        asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 2) : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
         __syncthreads();
         if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_addr(Sa), b0 = smem_addr(Sb);
+            const uint32_t a0 = smem_addr(buf(kt)), b0 = a0 + kTileA;
             const uint32_t lbo_a = (kBM / 8) * 128, lbo_b = (BN / 8) * 128;
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk) {
@@ -219,17 +228,31 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(
                     ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_addr(&bar[b])) : "memory");
+                         ::"r"(smem_addr(&bar[kt % kStages])) : "memory");
         }
         last = kt;
+        // refill: tile kt + kStages - 1 takes the buffer of tile kt - 1 once its MMAs completed
+        const int nt = kt + kStages - 1;
+        if (nt < nk) {
+            if (kt >= 1) {
+                const int t = kt - 1;
+                if (!__syncthreads_and(mbar_wait(&bar[t % kStages], (t / kStages) & 1, limit) ? 1 : 0)) {
+                    ok = false;
+                    break;
+                }
+            }
+            copy_tile(nt);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     // the last commit covers every MMA issued before it
     if (ok && nk > 0)
-        ok = __syncthreads_and(mbar_wait(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, limit) ? 1 : 0) != 0;
+        ok = __syncthreads_and(mbar_wait(&bar[(nk - 1) % kStages], ((nk - 1) / kStages) & 1, limit) ? 1 : 0) != 0;
     if (!ok) {
         if (threadIdx.x == 0) atomicExch(err, 1);
         // own MMAs may still run: wait (bounded) for the last commit before TMEM is freed
-        if (last >= 0) mbar_wait(&bar[last & 1], (last >> 1) & 1, limit);
+        if (last >= 0) mbar_wait(&bar[last % kStages], (last / kStages) & 1, limit);
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = m0 + warp * 32 + lane;
@@ -238,13 +261,25 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             if (row < M) {
+                const int col0 = n0 + c0;
+                float *dst = C + (long long)row * N + col0;
+                if (add_bias) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int col = n0 + c0 + i;
-                    if (col < N) {
-                        const float x = v[i] + (add_bias ? bias[col] : 0.f);
-                        float *dst = C + (long long)row * N + col;
-                        if (accumulate) atomicAdd(dst, x); else *dst = x;
+                    for (int i = 0; i < 16; ++i) v[i] += (col0 + i < N) ? __ldg(bias + col0 + i) : 0.f;
+                }
+                if (col0 + 16 <= N && (N & 3) == 0) {   // 16-byte aligned: four vector stores
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 x = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        float4 *d4 = reinterpret_cast<float4 *>(dst) + q;
+                        if (accumulate) atomicAdd(d4, x); else *d4 = x;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        if (col0 + i < N) {
+                            if (accumulate) atomicAdd(dst + i, v[i]); else dst[i] = v[i];
+                        }
                     }
                 }
             }
@@ -254,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                      : "memory");
     }
 }
