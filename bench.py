@@ -41,6 +41,10 @@ from paper_2509_25840_b300 import inputs  # noqa: E402
 
 ELEM_ACCESSES_PER_CELL_STEP = 11      # Horner-form RK4: 2 + 3 + 3 + 3 element accesses
 ELEM_ACCESSES_TEXTBOOK = 16           # the three-array k1..k4 form: 3 + 5 + 5 + 3
+# floating-point operations of one cell-stage of the two-mode stage kernel, an FMA counted as 2:
+# four 7-point derivatives (7 each), the Liouvillian sum (6), damping (3), on average 8/3 hierarchy
+# links of 5 for depth 4, and the RK4 combine (2)
+FLOPS_PER_CELL_STAGE_D2 = 52
 # launch shapes of the RK4 stage kernel the library's autotuner chooses from (variant index ->
 # points per thread, threads per block, minimum resident blocks per SM), as in stage_launch.cuh
 STAGE_SHAPES = {0: (2, 128, 8), 1: (2, 256, 4), 2: (2, 128, 6), 3: (4, 128, 4), 4: (4, 128, 4), 5: (4, 128, 4),
@@ -435,6 +439,37 @@ def run_ours(args, rank, world, local, pg):
                "fp64_pinned_by": "tests/test_gpu_parity.py: the FP64 build on this workload's "
                                  "model and grid against the FP64 CPU oracle"}
 
+    # ---- the FP64 path against the measured FP64 ALU peak (and the FP32 stage kernel's FLOP rate
+    #      against the FP32 peak, for its arithmetic intensity) -----------------------------------
+    alu = None
+    if rank == 0:
+        p64 = chfpe.alu_peak(64, stream.cuda_stream)
+        p32 = chfpe.alu_peak(32, stream.cuda_stream)
+        with chfpe.Handle(wl.model, wl.grid, depth=wl.depth, dt=wl.dt, precision=64,
+                          stream=stream.cuda_stream) as h64:
+            with torch.cuda.stream(stream):
+                x64 = torch.tensor(Weq_host, dtype=torch.float64, device=dev).unsqueeze(0)
+            torch.cuda.synchronize(dev)
+            h64.rk4_device(x64.data_ptr(), 1, 2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h64.rk4_device(x64.data_ptr(), 1, 10)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t64 = e0.elapsed_time(e1) / 1e3
+            del x64
+        fp64_rate = wl.cells * 10 / t64
+        fp64_flops = fp64_rate * 4 * FLOPS_PER_CELL_STAGE_D2
+        fp32_flops = value / world * 4 * FLOPS_PER_CELL_STAGE_D2
+        alu = {"fp64_peak_tflops": p64 / 1e12, "fp32_peak_tflops": p32 / 1e12,
+               "flops_per_cell_stage": FLOPS_PER_CELL_STAGE_D2,
+               "fp64_stage": {"cell_updates_per_s": fp64_rate, "tflops": fp64_flops / 1e12,
+                              "frac_of_fp64_peak": fp64_flops / p64,
+                              "how": "10 FP64 RK4 steps of one 32^4 x 15 state (chfpe_rk4_device, "
+                                     "CUDA events)"},
+               "fp32_stage_tflops": fp32_flops / 1e12, "fp32_stage_frac_of_fp32_peak": fp32_flops / p32,
+               "peak_how": "chfpe_alu_peak: eight independent FMA chains per thread, every SM"}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         rate, dt, threads, _ = oracle_sample(wl, 16)
@@ -463,6 +498,7 @@ def run_ours(args, rank, world, local, pg):
             "spectrum": spectrum,
             "plain_form": plain,
             "error_vs_fp64": err,
+            "alu": alu,
             "finite": finite,
         }
         print(json.dumps(line), flush=True)

@@ -407,6 +407,13 @@ chfpe_status chfpe_stats_reset(chfpe_handle *h, int time_stages);
 /* Synchronise the handle's stream and read the counters. */
 chfpe_status chfpe_stats_get(chfpe_handle *h, chfpe_stats *out);
 
+/* FMA throughput of the GPU's FP64 (precision 64) or FP32 (precision 32) ALUs in FLOP/s (an FMA
+ * counts 2): a microbenchmark kernel of eight independent FMA chains per thread filling every SM,
+ * fastest of three timed launches after a warm-up, on `stream` (NULL: the default stream),
+ * synchronous.  The denominator against which the FP64 paths (equilibration, the FP64 check
+ * build) are reported; the paper has no counterpart.  CHFPE_EINVAL, CHFPE_ECUDA. */
+chfpe_status chfpe_alu_peak(int precision, void *stream, double *flops);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *chfpe_last_error(void);
 

@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
                              ctypes.c_int, ctypes.c_double, _DP, _VP], S),
         "chfpe_stats_reset": ([_H, ctypes.c_int], S),
         "chfpe_stats_get": ([_H, ctypes.POINTER(chfpe_stats)], S),
+        "chfpe_alu_peak": ([ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double)], S),
         "chfpe_last_error": ([], ctypes.c_char_p),
         "chfpe_stage_tuning": ([_H, ctypes.POINTER(ctypes.c_int), _DP], S),
         "chfpe_surrogate_param_count": ([], ctypes.c_longlong),
@@ -149,6 +150,13 @@ def load(path: str = LIB_PATH):
         fn.restype = res
     _lib = lib
     return lib
+
+
+def alu_peak(precision: int, stream: int | None = None) -> float:
+    """chfpe_alu_peak: measured FMA throughput of the FP64 or FP32 ALUs in FLOP/s."""
+    out = ctypes.c_double(0.0)
+    _check(load().chfpe_alu_peak(int(precision), stream, ctypes.byref(out)))
+    return out.value
 
 
 def last_error() -> str:

@@ -492,3 +492,14 @@ def test_response3_matches_oracle(d, n, depth, dt, stride, n2, nt, mb):
             h.set_equilibrium(Weq)
             got = h.response3(mu, Pi, Pi, mu, nt, n2, nt, stride)
         assert _norm_err(got, want) < tol, (prec, _norm_err(got, want))
+
+
+def test_alu_peak_microbenchmark():
+    """chfpe_alu_peak: positive FMA rates, FP32 above FP64, both below a generous physical bound
+    (2 flops x 148 SMs x 256 lanes x 2.1 GHz)."""
+    chfpe = _chfpe()
+    p64, p32 = chfpe.alu_peak(64), chfpe.alu_peak(32)
+    bound = 2 * 148 * 256 * 2.1e9
+    assert 0 < p64 < p32 < bound, (p64, p32)
+    with pytest.raises(chfpe.ChfpeError):
+        chfpe.alu_peak(16)
