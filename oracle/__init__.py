@@ -29,8 +29,8 @@ Parity status per function (what pins it; the pins live in ``tests/test_oracle_p
   h_*          (Hermite-function momenta, Appendix A) the antisymmetry of the ladder generator,
                Boltzmann stationarity, the Brownian closed form, the moment closure, and the
                grid representation's responses on the same model; with qscheme = 1 (compact q
-               derivatives, Sec. III B) the Brownian closed form, Boltzmann stationarity and
-               convergence to the explicit scheme's limit
+               derivatives, Sec. III B) the Brownian closed form and Boltzmann stationarity;
+               with qscheme = 2 (its skew-symmetric part) also the antisymmetry of the generator
   compact_deriv1d  exactness on polynomials of degree <= 6 away from the ends, the scheme's
                closed-form Fourier symbol, the truncation-error constant against the explicit
                stencil (1/9 of it), decay of the end effect at the rate of A's Green's function
@@ -103,6 +103,7 @@ def _load():
             lib.orc_dUdq.restype = ctypes.c_double
             lib.orc_deriv1d.argtypes = [ctypes.c_long, ctypes.c_double, _DP, _DP]
             lib.orc_compact_deriv1d.argtypes = [ctypes.c_long, ctypes.c_double, _DP, _DP]
+            lib.orc_compact_skew_deriv1d.argtypes = [ctypes.c_long, ctypes.c_double, _DP, _DP]
             lib.orc_rhs.argtypes = [P, _DP, _DP]
             lib.orc_rk4.argtypes = [P, _DP, ctypes.c_double, ctypes.c_long]
             lib.orc_insert.argtypes = [P, O, _DP, _DP]
@@ -232,6 +233,14 @@ def compact_deriv1d(f, h: float) -> np.ndarray:
     f = np.ascontiguousarray(f, dtype=np.float64)
     out = np.empty_like(f)
     _load().orc_compact_deriv1d(f.size, float(h), _p(f), _p(out))
+    return out
+
+
+def compact_skew_deriv1d(f, h: float) -> np.ndarray:
+    """The skew-symmetric part (A^{-1} B + B A^{-1}) f / 2h of the compact derivative."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty_like(f)
+    _load().orc_compact_skew_deriv1d(f.size, float(h), _p(f), _p(out))
     return out
 
 

@@ -66,7 +66,8 @@ typedef struct {
     int nq[3], np[3];
     double qmin[3], qmax[3], pmin[3], pmax[3];
     int qscheme;         /* q-derivatives of the Hermite representation: 0 = the explicit
-                            6th-order central difference, 1 = the compact scheme of Sec. III B */
+                            6th-order central difference, 1 = the compact scheme of Sec. III B,
+                            2 = its skew-symmetric part (orc_compact_skew_deriv1d) */
 } orc_problem;
 
 typedef struct {
@@ -296,6 +297,35 @@ void orc_compact_deriv1d(long n, double h, const double *f, double *out)
     }
     for (long i = n - 2; i >= 0; --i) out[i] -= cp[i] * out[i + 1];
     free(cp);
+}
+
+/* The skew-symmetric part of the compact derivative: (A^{-1} B + B A^{-1}) f / (2 h).  With the
+ * truncated end rows of Sec. III B, A^{-1} B is not antisymmetric (A and B do not commute near the
+ * ends), and in the hierarchy's generator that non-antisymmetric part gives growing modes; this
+ * operator is antisymmetric (B^T = -B, A^T = A) and equals the compact derivative wherever the end
+ * effects have decayed (they fall off by 0.38 per point).  Two tridiagonal solves (Thomas). */
+void orc_compact_skew_deriv1d(long n, double h, const double *f, double *out)
+{
+    const double alpha = 1.0 / 3.0, a = 7.0 / 9.0, b = 1.0 / 36.0;
+    double *x1 = malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *y = malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *cp = malloc(sizeof(double) * (n > 0 ? n : 1));
+    orc_compact_deriv1d(n, h, f, x1);                 /* A^{-1} B f / h */
+    for (long i = 0; i < n; ++i) y[i] = f[i];         /* A^{-1} f */
+    for (long i = 0; i < n; ++i) {
+        double sub = (i >= 1) ? alpha : 0.0;
+        double sup = (i + 1 < n) ? alpha : 0.0;
+        double piv = 1.0 - ((i >= 1) ? sub * cp[i - 1] : 0.0);
+        cp[i] = sup / piv;
+        y[i] = (y[i] - ((i >= 1) ? sub * y[i - 1] : 0.0)) / piv;
+    }
+    for (long i = n - 2; i >= 0; --i) y[i] -= cp[i] * y[i + 1];
+    for (long i = 0; i < n; ++i) {                    /* B A^{-1} f / h, then the mean */
+        double y1p = (i + 1 < n) ? y[i + 1] : 0.0, y1m = (i >= 1) ? y[i - 1] : 0.0;
+        double y2p = (i + 2 < n) ? y[i + 2] : 0.0, y2m = (i >= 2) ? y[i - 2] : 0.0;
+        out[i] = 0.5 * (x1[i] + (a * (y1p - y1m) + b * (y2p - y2m)) / h);
+    }
+    free(x1); free(y); free(cp);
 }
 
 /* the same derivative along axis a of one member's field, at point x */
@@ -636,7 +666,7 @@ int orc_response2(const orc_problem *pr, const orc_optical *A, const orc_optical
  * Phi link and the insertion use, (d/dp + p/2mkT) the matching lowering operator.  Coefficients
  * with k_s outside [0, K_s) are zero (truncation).  d/dq_s is the same 6th-order central
  * difference with zero values outside the q-grid (qscheme 0), or the compact scheme of
- * Sec. III B, orc_compact_deriv1d (qscheme 1).
+ * Sec. III B, orc_compact_deriv1d (qscheme 1), or its skew-symmetric part (qscheme 2).
  *
  * Layout: [member][q_1]..[q_d][k_1]..[k_d], k_d fastest; the orc_problem's np[s] holds K_s
  * (pmin/pmax are not used).
@@ -679,7 +709,7 @@ static double hderiv_q(const orc_geom *g, const double *C, int i, long x, const 
 
 /* the compact derivative (Sec. III B) of every member's coefficients along every q axis, line by
  * line: D[(s M + i) P + x] = d/dq_s c^(i) at x.  NULL when out of memory. */
-static double *h_compact_derivs(const orc_geom *g, const double *C)
+static double *h_compact_derivs(const orc_geom *g, const double *C, int skew)
 {
     const int d = g->d;
     const long P = g->P;
@@ -700,7 +730,10 @@ static double *h_compact_derivs(const orc_geom *g, const double *C)
                     continue;
                 }
                 for (long j = 0; j < n; ++j) f[j] = C[(long)i * P + x0 + j * st];
-                orc_compact_deriv1d(n, g->h[s], f, df);
+                if (skew)
+                    orc_compact_skew_deriv1d(n, g->h[s], f, df);
+                else
+                    orc_compact_deriv1d(n, g->h[s], f, df);
                 for (long j = 0; j < n; ++j) D[((long)s * g->M + i) * P + x0 + j * st] = df[j];
                 free(f); free(df);
             }
@@ -718,8 +751,8 @@ int orc_h_rhs(const orc_problem *pr, const double *Cin, double *K)
     const long P = g.P;
     const double kT = pr->kT;
     double *Dpre = NULL;
-    if (pr->qscheme == 1) {
-        Dpre = h_compact_derivs(&g, Cin);
+    if (pr->qscheme == 1 || pr->qscheme == 2) {
+        Dpre = h_compact_derivs(&g, Cin, pr->qscheme == 2);
         if (!Dpre) return -3;
     } else if (pr->qscheme != 0) {
         return -1;

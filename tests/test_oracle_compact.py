@@ -130,3 +130,63 @@ def test_hermite_compact_boltzmann_stationary_at_sixth_order(d, ns, K, L):
         res.append(np.abs(oracle.h_rhs(pb, c)).max() / np.abs(c).max())
     order = math.log(res[0] / res[1]) / math.log(ns[1] / ns[0])
     assert res[1] < 1e-3 and order > 4.5, (res, order)
+
+
+def _generator(pb):
+    N = pb.M * pb.P
+    M = np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        M[:, j] = oracle.h_rhs(pb, e.reshape(pb.state_shape)).ravel()
+    return M
+
+
+def _anharmonic_sl():
+    return inputs.Model(nmodes=1, kT=1.0, m=(1.0,), omega=(1.0,), g4=(0.05,), zeta=(0.2,),
+                        gamma=(1.0,), V_LL=(1.0,), V_SL=(0.3,))
+
+
+def test_printed_end_rows_give_a_growing_mode_and_the_skew_part_does_not():
+    """With the printed (truncated) end rows, A^{-1} B is not antisymmetric; inside the Hermite
+    generator (anharmonic mode, square-linear coupling, 32 q points, K = 6, depth 3) that gives an
+    eigenvalue with Re > 0.01, i.e. a mode that grows over a spectrum's t ~ 25.  The skew-symmetric
+    part (qscheme 2) makes the generator antisymmetric minus the damping, like the explicit
+    stencil: M + M^T = -2 diag(sum_s n_s gamma_s)."""
+    model = _anharmonic_sl()
+    L = inputs.default_grid(model, [32]).qmax[0]
+    grid = _hgrid([32], [6], [L])
+    M1 = _generator(oracle.Problem(model, grid, 3, qscheme=1))
+    assert np.linalg.eigvals(M1).real.max() > 1e-2
+    pb2 = oracle.Problem(model, grid, 3, qscheme=2)
+    M2 = _generator(pb2)
+    damp = np.repeat([n[0] * model.gamma[0] for n in oracle.members(1, 3)], pb2.P)
+    np.testing.assert_allclose(M2 + M2.T, -2.0 * np.diag(damp), atol=1e-12)
+    assert np.linalg.eigvals(M2).real.max() < 1e-9
+
+
+def test_skew_part_is_antisymmetric_and_equals_the_compact_derivative_inside():
+    n, h = 64, 0.1
+    D = np.stack([oracle.compact_skew_deriv1d(np.eye(n)[j], h) for j in range(n)], axis=1)
+    np.testing.assert_allclose(D + D.T, 0.0, atol=1e-13)
+    x = np.linspace(-1.0, 1.0, 160)
+    p = np.polynomial.Polynomial(np.random.default_rng(7).normal(size=7))
+    ds = oracle.compact_skew_deriv1d(p(x), x[1] - x[0])
+    dc = oracle.compact_deriv1d(p(x), x[1] - x[0])
+    scale = np.abs(p.deriv()(x)).max()
+    assert np.abs(ds - p.deriv()(x))[70:90].max() < 5e-14 * scale   # sixth order, away from the ends
+    assert np.abs(ds - dc)[70:90].max() < 5e-14 * scale
+
+
+def test_hermite_skew_compact_r1_brownian_closed_form():
+    model, (m, w, kT, zeta, gamma, V) = _harmonic()
+    dt, nt, stride = 0.01, 11, 20
+    want = -ref.g_discrete(ref.brownian_matrix(m, w, zeta, gamma, V), dt, [k * stride for k in range(nt)])
+    mu = inputs.Optical(lin=(1.0,))
+    sq = math.sqrt(kT / (m * w * w))
+    errs = []
+    for n in (48, 96):
+        pb = oracle.Problem(model, _hgrid([n], [4], [8 * sq]), 3, qscheme=2)
+        R = oracle.h_response1(pb, mu, mu, oracle.h_boltzmann(pb), dt, nt, stride)
+        errs.append(np.abs(R - want).max() / np.abs(want).max())
+    assert errs[1] < 1e-7 and math.log2(errs[0] / errs[1]) > 5.5, errs
