@@ -70,11 +70,16 @@ def parse():
                     help="skip the whole-spectrum run (spectra/s and the end-to-end figure)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="two_mode_32",
-                    choices=["two_mode_32", "one_mode_64", "three_mode_20", "sweep"],
+                    choices=["two_mode_32", "one_mode_64", "three_mode_20", "sweep",
+                             "two_mode_hermite"],
                     help="two_mode_32 is the benchmark; the others are secondary measurements")
     ap.add_argument("--instances", type=int, default=64, help="sweep: instances in the batch")
     ap.add_argument("--error-instances", type=int, default=8,
                     help="sweep: instances re-run in FP64 for the per-instance error report")
+    ap.add_argument("--hermite-k", type=int, default=10,
+                    help="two_mode_hermite: Hermite functions per mode")
+    ap.add_argument("--q-scheme", type=int, default=0, choices=[0, 1, 2],
+                    help="two_mode_hermite: q-derivatives, 0 explicit stencil, 1 compact (PCR), 2 its skew part")
     ap.add_argument("--profile-case", action="store_true",
                     help="run `--steps` RK4 steps of `--batch` random states of the workload "
                          "through chfpe_rk4_device (a small, fixed case for ncu)")
@@ -567,6 +572,26 @@ def run_extra(args, local):
                 " dt=0.002, TRT R2 on %dx%d at dtau=0.1 (the 128x128 spectrum needs %d state-steps)"
                 % (nt, nt, full.r2_state_steps()))
         unit_name = "R2 spectra (reduced t-grid)"
+    elif args.workload == "two_mode_hermite":
+        base = inputs.two_mode_32(nt=args.nt)
+        K = args.hermite_k
+        hgrid = inputs.Grid(nq=base.grid.nq, np=(K, K), qmin=base.grid.qmin, qmax=base.grid.qmax,
+                            pmin=(0.0, 0.0), pmax=(1.0, 1.0))
+        prec, dtype = 32, "f32"
+        nt = args.nt
+        h = chfpe.Handle(base.model, hgrid, depth=base.depth, dt=base.dt, precision=prec,
+                         max_batch=nt, stream=stream.cuda_stream, p_basis=1, q_scheme=args.q_scheme)
+        eq = h.equilibrate(args.eq_steps, 1e-10, max(1, args.eq_steps))
+        hcells = h.members * h.points
+        units = hcells * base.r2_state_steps()
+        step = lambda: h.response2(base.A, base.B, base.C, nt, nt, base.stride)
+        desc = ("two_mode_hermite: the two_mode_32 model and q grid (32 x 32) with the momenta in %d x %d "
+                "Hermite functions (Sec. III A, Appendix A), %s q-derivatives, depth 4, dt=0.005; R2 on "
+                "%dx%d at dtau=0.2, all t1 branches batched; %d cells per state against %d on the "
+                "32^4 grid" % (K, K, {0: "explicit 6th-order", 1: "compact (Sec. III B, PCR)",
+                               2: "skew-symmetric compact (Sec. III B, two PCR solves)"}[args.q_scheme],
+                              nt, nt, hcells, base.cells))
+        unit_name = "R2 spectra"
     else:
         n = args.instances
         wls = [inputs.sweep_instance(s) for s in range(n)]
@@ -616,6 +641,28 @@ def run_extra(args, local):
     if args.workload == "three_mode_20":
         line["extrapolated_s_per_128x128_spectrum"] = (inputs.three_mode_20().r2_state_steps() *
                                                         wl.cells / (units * args.steps / T))
+    if args.workload == "two_mode_hermite" and args.err_nt > 0:
+        # the Hermite representation against the 32^4 grid representation of the same model and
+        # q grid (both FP64 on the GPU, each from its own equilibrium), and its FP32 path against
+        # its FP64 path
+        n = args.err_nt
+        Ceq = h.get_equilibrium()
+        R = {}
+        for prec_e in (32, 64):
+            with chfpe.Handle(base.model, hgrid, depth=base.depth, dt=base.dt, precision=prec_e,
+                              max_batch=n, stream=stream.cuda_stream, p_basis=1,
+                              q_scheme=args.q_scheme) as he:
+                he.set_equilibrium(Ceq)
+                R[prec_e] = he.response2(base.A, base.B, base.C, n, n, base.stride)
+        with chfpe.Handle(base.model, base.grid, depth=base.depth, dt=base.dt, precision=64,
+                          max_batch=n, stream=stream.cuda_stream) as hg:
+            hg.equilibrate(args.eq_steps, 1e-10, max(1, args.eq_steps))
+            Rg = hg.response2(base.A, base.B, base.C, n, n, base.stride)
+        line["error"] = {
+            "samples": "%dx%d at dtau=0.2 (t1, t2 <= %.1f)" % (n, n, (n - 1) * 0.2),
+            "f32_vs_f64": float(np.abs(R[32] - R[64]).max() / np.abs(R[64]).max()),
+            "hermite_f64_vs_grid_32^4_f64": float(np.abs(R[64] - Rg).max() / np.abs(Rg).max()),
+            "metric": "max |R2 - R2_ref| / max |R2_ref|"}
     if args.workload == "sweep" and args.error_instances > 0:
         # error of the FP32 + bf16-tier propagation against FP64, per instance: the first
         # instances, from the same stored equilibria, R1 over 200 steps (21 samples)

@@ -101,8 +101,11 @@ typedef struct {
                         /* stencil; 1 = the compact 6th-order scheme of Sec. III B (A f' = B f/h,*/
                         /* alpha = 1/3, a = 7/9, b = 1/36, zero values outside the q-grid),     */
                         /* tridiagonal systems solved by parallel cyclic reduction (Sec. III C);*/
-                        /* needs p_basis = 1 and at most 256 q points per axis; the handle then */
-                        /* holds max(1, max_batch) x nmodes derivative arrays of a state        */
+                        /* 2 = the skew-symmetric part (A^-1 B + B A^-1) / 2h of that operator  */
+                        /* (two PCR solves): with the printed end rows scheme 1 can give the    */
+                        /* hierarchy growing modes, scheme 2 cannot; needs p_basis = 1 and at   */
+                        /* most 256 q points per axis; the handle then holds                    */
+                        /* max(1, max_batch) x nmodes derivative arrays of a state              */
 } chfpe_options;
 
 /* Create a handle for one model on one grid.  Validates the structs, builds the coefficient

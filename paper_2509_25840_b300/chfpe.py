@@ -263,7 +263,8 @@ class Handle:
                  max_batch: int = 1, stream: int | None = None, bf16_tier: int = 0,
                  p_basis: int = 0, q_scheme: int = 0):
         """p_basis = 1: momenta in grid.np[s] Hermite functions (states hold coefficients);
-        q_scheme = 1 (with p_basis = 1): compact q-derivatives solved by PCR."""
+        q_scheme = 1 (with p_basis = 1): compact q-derivatives solved by PCR; 2: their
+        skew-symmetric part."""
         lib = load()
         self._m, self._g = make_model(model), make_grid(grid)
         self._o = chfpe_options(depth=int(depth), precision=int(precision), dt=float(dt),

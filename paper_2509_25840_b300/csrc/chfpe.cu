@@ -55,10 +55,12 @@ struct chfpe_handle {
     chfpe_options opts;
     int d = 0, depth = 0, M = 0, prec = 32;
     int basis = 0;              // 0: momenta on a uniform grid; 1: Hermite functions (np = K_s)
-    int qscheme = 0;            // Hermite momenta: 0 explicit q stencils, 1 compact (Sec. III B)
-    void *dq = nullptr;         // compact scheme: [dq_batch][d][M][P] q-derivatives (handle precision)
-    int dq_batch = 0;           // states one derivative pass covers
-    void *pcr = nullptr;        // compact scheme: PCR row multipliers per q axis (handle precision)
+    int qscheme = 0;            // Hermite momenta: 0 explicit q stencils, 1 compact (Sec. III B),
+                                // 2 the compact scheme's skew-symmetric part
+    void *dq = nullptr;         // compact scheme: [batch][d][M][P] q-derivatives of the stage's
+    size_t dq_bytes = 0;        // element type (FP64 stages of FP32 handles: equilibration)
+    void *pcr = nullptr;        // compact scheme: PCR row multipliers per q axis, FP64
+    void *pcr32 = nullptr;      // the same in FP32 (FP32 handles)
     long long pcr_off[3] = {0}; // element offset of axis s's table
     int pcr_levels[3] = {0};
     int P = 0, Pp = 0, NQ = 0;
@@ -251,13 +253,14 @@ static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *
             ++h->launches;
             return CHFPE_OK;
         }
-        // compact q-derivatives: per chunk of dq_batch states, one PCR pass per q axis into the
+        // compact q-derivatives: per chunk of states the derivative arrays hold, one PCR pass per q axis into the
         // derivative arrays, then the stage kernel reading them
         const long long sbytes = a.state_bytes;
         a.dq = (const T *)h->dq;
         a.dq_state = h->state;
-        for (int b0 = 0; b0 < batch; b0 += h->dq_batch) {
-            const int nb = std::min(h->dq_batch, batch - b0);
+        const int cap = (int)(h->dq_bytes / ((size_t)h->d * h->state * sizeof(T)));   // >= 1
+        for (int b0 = 0; b0 < batch; b0 += cap) {
+            const int nb = std::min(cap, batch - b0);
             const long long off = (long long)b0 * sbytes;
             for (int s = 0; s < h->d; ++s) {
                 HDerivArgs<T> da;
@@ -269,7 +272,8 @@ static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *
                 da.st = h->st[s];
                 da.lines = (int)(h->state / h->n[s]);
                 da.levels = h->pcr_levels[s];
-                da.coef = (const T *)h->pcr + h->pcr_off[s];
+                da.coef = (const T *)(sizeof(T) == 8 ? h->pcr : h->pcr32) + h->pcr_off[s];
+                da.skew = h->qscheme == 2 ? 1 : 0;
                 launch_hderiv<T>(da, nb, h->stream);
                 CK(cudaGetLastError());
                 ++h->launches;
@@ -679,9 +683,9 @@ static chfpe_status validate(const chfpe_model *m, const chfpe_grid *g, const ch
     if (o->p_basis != 0 && o->p_basis != 1) return fail(CHFPE_EINVAL, "p_basis must be 0 (grid) or 1 (Hermite)");
     if (o->p_basis == 1 && o->bf16_tier > 0)
         return fail(CHFPE_EINVAL, "bf16 tiers are built for grid momenta only");
-    if (o->q_scheme != 0 && o->q_scheme != 1)
-        return fail(CHFPE_EINVAL, "q_scheme must be 0 (explicit) or 1 (compact)");
-    if (o->q_scheme == 1) {
+    if (o->q_scheme < 0 || o->q_scheme > 2)
+        return fail(CHFPE_EINVAL, "q_scheme must be 0 (explicit), 1 (compact) or 2 (compact, skew part)");
+    if (o->q_scheme != 0) {
         if (o->p_basis != 1) return fail(CHFPE_EINVAL, "the compact q scheme is built for Hermite momenta (p_basis 1)");
         for (int s = 0; s < m->nmodes; ++s)
             if (g->nq[s] > 256) return fail(CHFPE_EINVAL, "the compact q scheme takes at most 256 q points per axis");
@@ -717,7 +721,7 @@ extern "C" void chfpe_destroy(chfpe_handle *h) {
     if (h->borrowed_arenas) h->cy = h->ca = h->cb = h->eq = nullptr;
     void *ptrs[] = {h->U_d, h->F_d, h->F_f, h->wp, h->CWq, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
                     h->cy, h->ca, h->cb, h->by, h->ba, h->bb, h->eq, h->stage64, h->partial, h->dR,
-                    h->counter, h->d_err, h->d_bar, h->d_geo, h->dq, h->pcr};
+                    h->counter, h->d_err, h->d_bar, h->d_geo, h->dq, h->pcr, h->pcr32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->lv_ptr.empty()) {            // work lists still owned by d_work (set-up failed)
@@ -839,8 +843,10 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
     for (void **p : barenas)
         if (!st && opts->max_batch > 0) *p = (void *)dalloc<char>(sbytes * opts->max_batch, &st);
     if (!st && h->qscheme) {
-        h->dq_batch = std::max(1, opts->max_batch);
-        h->dq = (void *)dalloc<char>((size_t)h->dq_batch * d * h->state * h->esize, &st);
+        // max(1, max_batch) states in the handle's precision, and at least one FP64 state (the
+        // FP64 equilibration of an FP32 handle runs through the same arrays)
+        h->dq_bytes = (size_t)d * h->state * std::max<size_t>((size_t)std::max(1, opts->max_batch) * h->esize, 8);
+        h->dq = (void *)dalloc<char>(h->dq_bytes, &st);
         // PCR tables (Sec. III C) of A = tridiag(1/3, 1, 1/3) per q axis, in FP64, then stored in
         // the handle precision: [levels][2][n] multipliers, [n] 1 / (b_i h)
         std::vector<double> tab;
@@ -873,22 +879,22 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
                 tab.insert(tab.end(), k2.begin(), k2.end());
             }
             for (int i = 0; i < n; ++i) tab.push_back(1.0 / (di[i] * h->h[s]));
-            const cudaError_t ce = h->prec == 64 ? configure_hderiv<double>(n) : configure_hderiv<float>(n);
+            cudaError_t ce = configure_hderiv<double>(n);
+            if (ce == cudaSuccess && h->prec == 32) ce = configure_hderiv<float>(n);
             if (ce != cudaSuccess) st = fail(CHFPE_ECUDA, std::string("PCR shared memory: ") + cudaGetErrorString(ce));
         }
-        if (!st) {
-            if (h->prec == 64) {
-                double *t = dalloc<double>(tab.size(), &st);
-                if (!st && cudaMemcpy(t, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
-                    st = fail(CHFPE_ECUDA, "PCR table upload");
-                h->pcr = t;
-            } else {
-                std::vector<float> tf(tab.begin(), tab.end());
-                float *t = dalloc<float>(tf.size(), &st);
-                if (!st && cudaMemcpy(t, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-                    st = fail(CHFPE_ECUDA, "PCR table upload");
-                h->pcr = t;
-            }
+        if (!st) {   // FP64 tables always (equilibration), FP32 ones for FP32 handles
+            double *t = dalloc<double>(tab.size(), &st);
+            if (!st && cudaMemcpy(t, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+                st = fail(CHFPE_ECUDA, "PCR table upload");
+            h->pcr = t;
+        }
+        if (!st && h->prec == 32) {
+            std::vector<float> tf(tab.begin(), tab.end());
+            float *t = dalloc<float>(tf.size(), &st);
+            if (!st && cudaMemcpy(t, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                st = fail(CHFPE_ECUDA, "PCR table upload");
+            h->pcr32 = t;
         }
     }
     if (st) { chfpe_destroy(h); return st; }

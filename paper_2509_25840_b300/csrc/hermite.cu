@@ -17,7 +17,7 @@ void launch_one(const HStageArgs<T> &a, int batch, cudaStream_t s) {
 }
 
 template <typename T>
-size_t deriv_smem(int n) { return (size_t)2 * n * kPcrCols * sizeof(T); }
+size_t deriv_smem(int n, bool skew) { return (size_t)(skew ? 3 : 2) * n * kPcrCols * sizeof(T); }
 
 // largest dynamic shared memory opted into so far, per element type
 template <typename T>
@@ -28,18 +28,24 @@ size_t &deriv_configured() {
 
 template <typename T>
 cudaError_t configure_deriv(int n) {
-    const size_t smem = deriv_smem<T>(n);
+    const size_t smem = deriv_smem<T>(n, true);   // the larger of the two kernels' needs
     if (smem <= deriv_configured<T>()) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(hderiv_pcr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(hderiv_pcr_kernel<T, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(hderiv_pcr_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
     if (e == cudaSuccess) deriv_configured<T>() = smem;
     return e;
 }
 
 template <typename T>
 void launch_deriv(const HDerivArgs<T> &a, int batch, cudaStream_t s) {
-    hderiv_pcr_kernel<T><<<dim3((a.lines + kPcrCols - 1) / kPcrCols, batch), dim3(kPcrCols, kPcrRows),
-                           deriv_smem<T>(a.n), s>>>(a);
+    const dim3 grid((a.lines + kPcrCols - 1) / kPcrCols, batch), block(kPcrCols, kPcrRows);
+    if (a.skew)
+        hderiv_pcr_kernel<T, true><<<grid, block, deriv_smem<T>(a.n, true), s>>>(a);
+    else
+        hderiv_pcr_kernel<T, false><<<grid, block, deriv_smem<T>(a.n, false), s>>>(a);
 }
 
 template <typename T>

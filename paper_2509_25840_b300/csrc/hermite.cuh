@@ -68,32 +68,26 @@ struct HDerivArgs {
     int levels;                 // PCR levels, 2^levels >= n
     const T *coef;              // [levels][2][n] row multipliers (rows i - 2^l, i + 2^l), then
                                 // [n] 1 / (b_i h) of the reduced diagonal
+    int skew;                   // 1: the skew-symmetric part of the compact derivative
 };
 
 constexpr int kPcrCols = 32, kPcrRows = 8;
 
-// compact first derivative along one q axis of a tile of 32 lines of every state in the batch
-// (blockIdx.y): load, B f, PCR, scale, store; 2 n 32 values of shared memory
+// (B f)_i = a (f_{i+1} - f_{i-1}) + b (f_{i+2} - f_{i-2}) of column tx of a shared tile, zero
+// values outside the line
 template <typename T>
-__global__ void __launch_bounds__(kPcrCols * kPcrRows) hderiv_pcr_kernel(const HDerivArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char pcr_smem[];
-    T *cur = reinterpret_cast<T *>(pcr_smem);
-    T *nxt = cur + a.n * kPcrCols;
-    const int tx = threadIdx.x, ty = threadIdx.y, n = a.n;
-    const int line = blockIdx.x * kPcrCols + tx;
-    const bool ok = line < a.lines;
-    const int outer = ok ? line / a.st : 0;
-    const long long base = (long long)outer * n * a.st + (ok ? line - outer * a.st : 0);
-    const T *f = reinterpret_cast<const T *>(a.in + (long long)blockIdx.y * a.in_state) + base;
-    for (int i = ty; i < n; i += kPcrRows) nxt[i * kPcrCols + tx] = ok ? __ldg(f + (long long)i * a.st) : T(0);
-    __syncthreads();
+__device__ __forceinline__ T pcr_bf(const T *F, int i, int n, int tx) {
     const T ca = T(7) / T(9), cb = T(1) / T(36);
-    for (int i = ty; i < n; i += kPcrRows) {
-        const T f1 = (i + 1 < n ? nxt[(i + 1) * kPcrCols + tx] : T(0)) - (i >= 1 ? nxt[(i - 1) * kPcrCols + tx] : T(0));
-        const T f2 = (i + 2 < n ? nxt[(i + 2) * kPcrCols + tx] : T(0)) - (i >= 2 ? nxt[(i - 2) * kPcrCols + tx] : T(0));
-        cur[i * kPcrCols + tx] = ca * f1 + cb * f2;
-    }
-    __syncthreads();
+    const T f1 = (i + 1 < n ? F[(i + 1) * kPcrCols + tx] : T(0)) - (i >= 1 ? F[(i - 1) * kPcrCols + tx] : T(0));
+    const T f2 = (i + 2 < n ? F[(i + 2) * kPcrCols + tx] : T(0)) - (i >= 2 ? F[(i - 2) * kPcrCols + tx] : T(0));
+    return ca * f1 + cb * f2;
+}
+
+// PCR on the columns of the shared tile `cur` (right-hand sides), `nxt` as scratch; returns the
+// buffer that holds the reduced right-hand sides d_i (x_i = d_i / b_i)
+template <typename T>
+__device__ __forceinline__ T *pcr_solve(T *cur, T *nxt, const HDerivArgs<T> &a, int tx, int ty) {
+    const int n = a.n;
     for (int l = 0; l < a.levels; ++l) {
         const int o = 1 << l;
         const T *k1 = a.coef + (long long)2 * l * n, *k2 = k1 + n;
@@ -108,10 +102,47 @@ __global__ void __launch_bounds__(kPcrCols * kPcrRows) hderiv_pcr_kernel(const H
         cur = nxt;
         nxt = t;
     }
-    const T *binv = a.coef + (long long)2 * a.levels * n;
-    if (ok) {
+    return cur;
+}
+
+// compact first derivative along one q axis of a tile of 32 lines of every state in the batch
+// (blockIdx.y): load, B f, PCR, scale, store; 2 n 32 values of shared memory.
+// SKEW: the skew-symmetric part (A^{-1} B f + B A^{-1} f) / 2h instead (3 n 32 values): the first
+// term as above, then a second PCR on f itself and B applied to its solution
+template <typename T, bool SKEW>
+__global__ void __launch_bounds__(kPcrCols * kPcrRows) hderiv_pcr_kernel(const HDerivArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char pcr_smem[];
+    T *buf0 = reinterpret_cast<T *>(pcr_smem);
+    T *buf1 = buf0 + a.n * kPcrCols;
+    T *buf2 = buf1 + a.n * kPcrCols;          // SKEW only
+    const int tx = threadIdx.x, ty = threadIdx.y, n = a.n;
+    const int line = blockIdx.x * kPcrCols + tx;
+    const bool ok = line < a.lines;
+    const int outer = ok ? line / a.st : 0;
+    const long long base = (long long)outer * n * a.st + (ok ? line - outer * a.st : 0);
+    const T *f = reinterpret_cast<const T *>(a.in + (long long)blockIdx.y * a.in_state) + base;
+    T *F = SKEW ? buf2 : buf1;                // f, kept while the first solve runs (SKEW)
+    for (int i = ty; i < n; i += kPcrRows) F[i * kPcrCols + tx] = ok ? __ldg(f + (long long)i * a.st) : T(0);
+    __syncthreads();
+    for (int i = ty; i < n; i += kPcrRows) buf0[i * kPcrCols + tx] = pcr_bf(F, i, n, tx);
+    __syncthreads();
+    const T *binv = a.coef + (long long)2 * a.levels * n;   // 1 / (b_i h)
+    T *x1 = pcr_solve(buf0, buf1, a, tx, ty);               // A^{-1} B f, unscaled
+    if constexpr (SKEW) {
+        // x1 lies in buf0 or buf1; the other one is scratch for the solve A y = f (f in buf2)
+        T *scratch = x1 == buf0 ? buf1 : buf0;
+        T *y = pcr_solve(buf2, scratch, a, tx, ty);         // A y = f: d_i, y_i = d_i / b_i
+        // y / h = d_i binv_i, in place; then out = (x1 binv + B (y / h)) / 2
+        for (int i = ty; i < n; i += kPcrRows) y[i * kPcrCols + tx] *= binv[i];
+        __syncthreads();
+        if (ok) {
+            T *o = a.out + (long long)blockIdx.y * a.out_state + base;
+            for (int i = ty; i < n; i += kPcrRows)
+                o[(long long)i * a.st] = T(0.5) * (x1[i * kPcrCols + tx] * binv[i] + pcr_bf(y, i, n, tx));
+        }
+    } else if (ok) {
         T *o = a.out + (long long)blockIdx.y * a.out_state + base;
-        for (int i = ty; i < n; i += kPcrRows) o[(long long)i * a.st] = cur[i * kPcrCols + tx] * binv[i];
+        for (int i = ty; i < n; i += kPcrRows) o[(long long)i * a.st] = x1[i * kPcrCols + tx] * binv[i];
     }
 }
 
@@ -271,7 +302,7 @@ template <>
 bool launch_hstage<double>(int d, int depth, const HStageArgs<double> &a, int batch, cudaStream_t s);
 
 // compact derivative along one q axis of `batch` states (hderiv_pcr_kernel); configure_hderiv
-// opts the kernel into the shared memory lines of n points need (once, before any launch or
+// opts the kernels into the shared memory lines of n points need (once, before any launch or
 // stream capture that uses them)
 template <typename T>
 cudaError_t configure_hderiv(int n);

@@ -45,7 +45,7 @@ def test_create_rejects_invalid_arguments_on_cpu():
         dict(max_batch=-1),
         dict(bf16_tier=2),             # not a compiled (modes, depth, tier) combination
         dict(q_scheme=1),              # the compact q scheme needs Hermite momenta
-        dict(p_basis=1, q_scheme=2),   # no such scheme
+        dict(p_basis=1, q_scheme=3),   # no such scheme
     ]
     for kw in bad:
         args = dict(depth=wl.depth, dt=wl.dt, precision=32, max_batch=1)

@@ -65,25 +65,27 @@ CASES = [
 ]
 
 
-def _handle(d, nq, K, depth, prec, max_batch=1, dt=0.003):
+def _handle(d, nq, K, depth, prec, max_batch=1, dt=0.003, qs=1):
     chfpe = _chfpe()
     model = _model(d)
     grid = _hgrid(nq, K)
     h = chfpe.Handle(model, grid, depth=depth, dt=dt, precision=prec, max_batch=max_batch,
-                     p_basis=1, q_scheme=1)
-    return h, oracle.Problem(model, grid, depth, qscheme=1)
+                     p_basis=1, q_scheme=qs)
+    return h, oracle.Problem(model, grid, depth, qscheme=qs)
 
 
 def _random(pb, seed):
     return inputs.uniform_array(seed, pb.M * pb.P).reshape(pb.state_shape)
 
 
+@pytest.mark.parametrize("qs", [1, 2])
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("d,nq,K,depth", CASES)
-def test_compact_rhs_matches_oracle(d, nq, K, depth, prec):
+def test_compact_rhs_matches_oracle(d, nq, K, depth, prec, qs):
     """The right-hand side of three seeded states at once (more states than the handle's
-    derivative arrays hold: the library works through them in chunks)."""
-    h, pb = _handle(d, nq, K, depth, prec, max_batch=2)
+    derivative arrays hold: the library works through them in chunks), for the compact scheme
+    (qs = 1) and its skew-symmetric part (qs = 2)."""
+    h, pb = _handle(d, nq, K, depth, prec, max_batch=2, qs=qs)
     with h:
         C = [_rounded(_random(pb, 31 + 7 * b + d), prec) for b in range(3)]
         want = [oracle.h_rhs(pb, c) for c in C]
@@ -96,10 +98,11 @@ def test_compact_rhs_matches_oracle(d, nq, K, depth, prec):
         assert np.abs(got[b] - want[b]).max() <= tol * np.abs(want[b]).max(), b
 
 
+@pytest.mark.parametrize("qs", [1, 2])
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("d,nq,K,depth", [CASES[0], CASES[3], CASES[5]])
-def test_compact_rk4_matches_oracle(d, nq, K, depth, prec):
-    h, pb = _handle(d, nq, K, depth, prec, max_batch=2)
+def test_compact_rk4_matches_oracle(d, nq, K, depth, prec, qs):
+    h, pb = _handle(d, nq, K, depth, prec, max_batch=2, qs=qs)
     with h:
         C = _rounded(_random(pb, 5) * 1e-2 + oracle.h_boltzmann(pb), prec)
         want = oracle.h_rk4(pb, C, 0.003, 20)
@@ -112,17 +115,18 @@ def test_compact_rk4_matches_oracle(d, nq, K, depth, prec):
     assert np.abs(got[1] + want).max() <= tol * scale
 
 
+@pytest.mark.parametrize("qs", [1, 2])
 @pytest.mark.parametrize("d,nq,K,depth,dt,stride,nt", [
     (1, [48], [8], 4, 0.005, 20, 12),
     (2, [12, 13], [6, 5], 3, 0.004, 30, 4),
 ])
-def test_compact_responses_match_oracle(d, nq, K, depth, dt, stride, nt):
+def test_compact_responses_match_oracle(d, nq, K, depth, dt, stride, nt, qs):
     """R1 and R2 (batched branches, chunks of 3) with compact q-derivatives: FP64 to 1e-10, FP32
     to 1e-4 of max|R| against the oracle (every branch propagated on its own)."""
     chfpe = _chfpe()
     model = _model(d)
     grid = _hgrid(nq, K)
-    pb = oracle.Problem(model, grid, depth, qscheme=1)
+    pb = oracle.Problem(model, grid, depth, qscheme=qs)
     Ceq = _rounded(oracle.h_boltzmann(pb), 32)
     mu = inputs.Optical(lin=(1.0, 0.6), quad=[[0.3, 0.1], [0.1, -0.2]])
     Pi = inputs.Optical(lin=(0.5, 1.0), quad=[[0.8, 0.0], [0.0, 0.4]])
@@ -130,7 +134,7 @@ def test_compact_responses_match_oracle(d, nq, K, depth, dt, stride, nt):
     w2 = oracle.h_response2(pb, mu, Pi, mu, Ceq, dt, nt, nt, stride)
     for prec, tol in ((64, 1e-10), (32, 1e-4)):
         with chfpe.Handle(model, grid, depth=depth, dt=dt, precision=prec, max_batch=3,
-                          p_basis=1, q_scheme=1) as h:
+                          p_basis=1, q_scheme=qs) as h:
             h.set_equilibrium(Ceq)
             r1 = h.response1(mu, mu, nt, stride)
             r2 = h.response2(mu, Pi, mu, nt, nt, stride)
@@ -159,3 +163,21 @@ def test_compact_r1_brownian_closed_form_on_the_gpu():
             err[n, qs] = np.abs(R - want).max() / np.abs(want).max()
     assert err[96, 1] < 1e-7 and math.log2(err[48, 1] / err[96, 1]) > 5.5, err
     assert err[48, 1] < err[48, 0] / 4, err
+
+
+@pytest.mark.parametrize("max_batch", [1, 4])
+@pytest.mark.parametrize("qs", [1, 2])
+def test_compact_fp64_equilibration_of_an_fp32_handle(qs, max_batch):
+    """An FP32 handle equilibrates in FP64 through the same derivative arrays and PCR tables
+    (FP64 copies of both): 100 FP64 steps from the sampled Boltzmann coefficients against the
+    oracle's h_rk4; the handle keeps its equilibrium in FP32, so every value agrees to the FP32
+    rounding of the FP64 result (half an ulp, 2^-24 relative, plus 1e-12 of the maximum for the
+    FP64 steps)."""
+    h, pb = _handle(2, [11, 16], [5, 6], 2, 32, max_batch=max_batch, qs=qs)
+    with h:
+        steps, res = h.equilibrate(100, 0.0, 50)
+        got = h.get_equilibrium()
+    want = oracle.h_rk4(pb, oracle.h_boltzmann(pb), 0.003, 100)
+    assert steps == 100
+    bound = 2.0 ** -24 * np.abs(want) * 1.01 + 1e-12 * np.abs(want).max()
+    assert np.all(np.abs(got - want) <= bound), np.abs(got - want).max()
