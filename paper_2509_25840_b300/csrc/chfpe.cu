@@ -1652,25 +1652,31 @@ static double bound_for(const chfpe_model *model, const chfpe_grid *grid, int de
 
 // one launch per non-empty work list (4-, 2- and 1-point tiles); the 4-point list exists only
 // for FP32 hierarchies the autotuner covers
-template <typename T, int D, int DEPTH, int M32>
-static void launch_batch_m(const chfpe_handle *b, const BatchStageArgs<T> &a0) {
+template <typename T, int D, int DEPTH, int M32, int ES>
+static void launch_batch_es(const chfpe_handle *b, const BatchStageArgs<T> &a0) {
     constexpr int M = member_count(D, DEPTH);
     constexpr int MINB = (sizeof(T) == 4 && M <= 15) ? 8 : 4;
     BatchStageArgs<T> a = a0;
     if constexpr (tunable(sizeof(T), D, DEPTH)) {
         if (b->nwork[0]) {
             a.work = b->d_work[0];
-            stage_batch_kernel<T, D, DEPTH, 4, 128, 4, M32><<<b->nwork[0], 128, 0, b->stream>>>(a);
+            stage_batch_kernel<T, D, DEPTH, 4, 128, 4, M32, ES><<<b->nwork[0], 128, 0, b->stream>>>(a);
         }
     }
     if (b->nwork[1]) {
         a.work = b->d_work[1];
-        stage_batch_kernel<T, D, DEPTH, kVec, 128, MINB, M32><<<b->nwork[1], 128, 0, b->stream>>>(a);
+        stage_batch_kernel<T, D, DEPTH, kVec, 128, MINB, M32, ES><<<b->nwork[1], 128, 0, b->stream>>>(a);
     }
     if (b->nwork[2]) {
         a.work = b->d_work[2];
-        stage_batch_kernel<T, D, DEPTH, 1, 128, 4, M32><<<b->nwork[2], 128, 0, b->stream>>>(a);
+        stage_batch_kernel<T, D, DEPTH, 1, 128, 4, M32, ES><<<b->nwork[2], 128, 0, b->stream>>>(a);
     }
+}
+
+// early stores in storage order (measured 1 % faster on 64 sweep instances: 737 against 728 GB/s)
+template <typename T, int D, int DEPTH, int M32>
+static void launch_batch_m(const chfpe_handle *b, const BatchStageArgs<T> &a0) {
+    launch_batch_es<T, D, DEPTH, M32, 1>(b, a0);
 }
 
 static int batch_lists(const chfpe_handle *b) {

@@ -589,7 +589,9 @@ struct BatchStageArgs {
     T c;
 };
 
-template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32>
+// ES = 1: each member stored as soon as its last contribution is in (storage order), as the
+// single-handle launch shapes with early stores
+template <typename T, int D, int DEPTH, int V, int NT, int MINB, int M32, int ES = 0>
 __global__ void __launch_bounds__(NT, MINB) stage_batch_kernel(const BatchStageArgs<T> b) {
     // the block's instance geometry, copied once into shared memory: every thread reads its
     // sizes, strides and coefficients many times
@@ -605,8 +607,8 @@ __global__ void __launch_bounds__(NT, MINB) stage_batch_kernel(const BatchStageA
     const int x0 = (item.y * NT + threadIdx.x) * V;
     if (x0 >= sg.g.P) return;
     const long long off = sg.off;
-    stage_points<T, D, DEPTH, V, M32>(sg.g, b.in + off, b.y ? b.y + off : nullptr, b.out + off,
-                                      b.stage >= 0 ? sg.cst[b.stage] : b.c, x0);
+    stage_points<T, D, DEPTH, V, M32, true, false, 0, ES>(sg.g, b.in + off, b.y ? b.y + off : nullptr,
+                                                         b.out + off, b.stage >= 0 ? sg.cst[b.stage] : b.c, x0);
 }
 
 // ------------------------------------------------------------------------------------------
