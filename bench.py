@@ -437,12 +437,48 @@ def run_ours(args, rank, world, local, pg):
                               max_batch=n, stream=stream.cuda_stream) as he:
                 he.set_equilibrium(Weq_host)
                 R[prec] = he.response2(wl.A, wl.B, wl.C, n, n, wl.stride)
+        R64_grid = R[64]
         e = float(np.abs(R[32] - R[64]).max() / np.abs(R[64]).max())
         err = {"metric": "max |R2_f32 - R2_f64| / max |R2_f64|", "value": e,
                "tolerance": 1e-4, "samples": "%dx%d at dtau=40 dt (t1, t2 <= %.2f)" % (
                    n, n, (n - 1) * wl.stride * wl.dt),
                "fp64_pinned_by": "tests/test_gpu_parity.py: the FP64 build on this workload's "
                                  "model and grid against the FP64 CPU oracle"}
+
+    # ---- the same spectrum in the paper's own representation: momenta in Hermite functions
+    #      (Sec. III A, Appendix A) on the same q grid, FP32, one whole 64 x 64 R2 -------------------
+    paper_rep = None
+    if rank == 0 and not args.no_spectrum:
+        K = 10
+        hgrid = inputs.Grid(nq=wl.grid.nq, np=(K, K), qmin=wl.grid.qmin, qmax=wl.grid.qmax,
+                            pmin=(0.0, 0.0), pmax=(1.0, 1.0))
+        with chfpe.Handle(wl.model, hgrid, depth=wl.depth, dt=wl.dt, precision=32, max_batch=nt1,
+                          stream=stream.cuda_stream, p_basis=1) as hh:
+            hh.equilibrate(args.eq_steps, 1e-10, max(1, args.eq_steps))
+            Ceq = hh.get_equilibrium()
+            hh.response2(wl.A, wl.B, wl.C, 2, 2, wl.stride)            # warm-up
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Rh = hh.response2(wl.A, wl.B, wl.C, nt1, nt2, wl.stride)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            th = e0.elapsed_time(e1) / 1e3
+            hcells = hh.members * hh.points
+        paper_rep = {"representation": "momenta in %d x %d Hermite functions, the same 32 x 32 q grid, "
+                                       "explicit q stencil (Sec. III A, Appendix A)" % (K, K),
+                     "cells_per_state": hcells, "s_per_spectrum": th, "spectra_per_s": 1.0 / th,
+                     "finite": bool(np.isfinite(Rh).all())}
+        if args.err_nt > 0:
+            n = args.err_nt
+            with chfpe.Handle(wl.model, hgrid, depth=wl.depth, dt=wl.dt, precision=64, max_batch=n,
+                              stream=stream.cuda_stream, p_basis=1) as hh:
+                hh.set_equilibrium(Ceq)
+                Rh64 = hh.response2(wl.A, wl.B, wl.C, n, n, wl.stride)
+            paper_rep["difference_vs_grid_f64"] = float(np.abs(Rh64 - R64_grid).max() /
+                                                        np.abs(R64_grid).max())
+            paper_rep["difference_how"] = ("max |R2_hermite_f64 - R2_grid_f64| / max |R2_grid_f64| on "
+                                           "%dx%d samples: the grid's momentum discretisation error" % (n, n))
 
     # ---- the FP64 path against the measured FP64 ALU peak (and the FP32 stage kernel's FLOP rate
     #      against the FP32 peak, for its arithmetic intensity) -----------------------------------
@@ -504,6 +540,7 @@ def run_ours(args, rank, world, local, pg):
             "plain_form": plain,
             "error_vs_fp64": err,
             "alu": alu,
+            "paper_representation": paper_rep,
             "finite": finite,
         }
         print(json.dumps(line), flush=True)
