@@ -304,3 +304,35 @@ def test_borrowed_instances_step_their_own_dt():
                 h.propagate(6)
                 want = h.get_state()
             assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("tier", [0, 3])
+def test_batch_rows_of_any_length_match_single_handles_and_oracle(tier):
+    """Odd last momentum extents (13, 15: 1-point tiles) beside a multiple of 4 (4-point tiles)
+    in one batch, FP32 (and BF16 tiers 3-4), depth 4, R1 over 40 steps: against single handles to
+    FP32 rounding and against the FP64 oracle to 1e-4."""
+    chfpe = _chfpe()
+    grids = [[12, 11, 10, 13], [9, 12, 10, 15], [9, 11, 7, 13], [10, 10, 12, 12]]
+    insts = []
+    for seed, n in zip((5, 6, 8, 9), grids):
+        wl = inputs.sweep_instance(seed)
+        insts.append((wl.model, inputs.default_grid(wl.model, n, cut=12.0, nsigma=5.0)))
+    depth, dt, nt, stride = 4, 0.004, 5, 10
+    mu = inputs.Optical(lin=(1.0, 1.0), quad=[[0.2, 0.0], [0.0, -0.1]])
+    Ws = [_eq(m, g, depth) for m, g in insts]
+    with chfpe.Batch([m for m, _ in insts], [g for _, g in insts], depth=depth, dt=dt,
+                     precision=32, bf16_tier=tier) as b:
+        for i in range(len(insts)):
+            b.instance(i).set_equilibrium(Ws[i])
+        R = b.response1_all(mu, mu, nt, stride)
+    for i, (m, g) in enumerate(insts):
+        W = Ws[i]
+        with chfpe.Handle(m, g, depth=depth, dt=dt, precision=32, bf16_tier=tier) as h:
+            h.set_equilibrium(W)
+            single = h.response1(mu, mu, nt, stride)
+        scale = np.abs(single).max()
+        assert np.abs(R[i] - single).max() <= 1e-6 * scale, (grids[i], np.abs(R[i] - single).max() / scale)
+        if tier == 0:
+            pb = oracle.Problem(m, g, depth)
+            want = oracle.response1(pb, mu, mu, W.astype(np.float32).astype(np.float64), dt, nt, stride)
+            assert np.abs(R[i] - want).max() <= 1e-4 * np.abs(want).max(), grids[i]
