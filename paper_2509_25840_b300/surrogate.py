@@ -72,6 +72,27 @@ def make_dataset(seeds, **solver_kw):
     return X, R, time.perf_counter() - t0
 
 
+def make_dataset_batched(seeds, n_axis: int = 16, depth: int = 2, dt: float = 0.005,
+                         stride: int = 40, nt: int = 64, eq_steps: int = 4000, group: int = 64,
+                         precision: int = 32):
+    """The same data as make_dataset, solved `group` parameter vectors at a time by one batch
+    (chfpe_create_batch: every instance's equilibration and R2 branches advance in the same
+    launches; an instance that needs a smaller step substeps on its own)."""
+    seeds = list(seeds)
+    X = np.stack([inputs.surrogate_params(s) for s in seeds])
+    R = np.empty((len(seeds), nt, nt))
+    mu = inputs.Optical(lin=(1.0, 1.0))
+    t0 = time.perf_counter()
+    for i0 in range(0, len(seeds), group):
+        xs = X[i0:i0 + group]
+        models = [inputs.surrogate_model(x) for x in xs]
+        grids = [inputs.default_grid(m, [n_axis] * 4) for m in models]
+        with chfpe.Batch(models, grids, depth=depth, dt=dt, precision=precision, max_batch=nt) as b:
+            b.equilibrate_all(eq_steps, 1e-10, 500)
+            R[i0:i0 + len(xs)] = b.response2_all(mu, mu, mu, nt, nt, stride)
+    return X, R, time.perf_counter() - t0
+
+
 def targets(R):
     """(normalised spectra as float32 [n][4096], log10 scale as float32 [n])."""
     R = np.asarray(R, dtype=np.float64).reshape(len(R), -1)
@@ -202,6 +223,9 @@ def main(argv=None):
     ap.add_argument("--generate-only", action="store_true",
                     help="solve and save the n-train + n-test spectra to --data, no training")
     ap.add_argument("--seed0", type=int, default=100000)
+    ap.add_argument("--batched", type=int, default=0,
+                    help="solve the data this many parameter vectors at a time in one batch "
+                         "(0: one handle per vector)")
     args = ap.parse_args(argv)
     chfpe.load()
     kw = dict(n_axis=args.n_axis, depth=args.depth)
@@ -210,6 +234,11 @@ def main(argv=None):
         d = np.load(args.data)
         X, R = d["X"], d["R"].astype(np.float64)
         t_solve, n_solved = float(d["t_solve"]), int(d["n_solved"])
+    elif args.batched > 0:
+        X, R, t_solve = make_dataset_batched(range(args.seed0, args.seed0 + n_all), group=args.batched, **kw)
+        n_solved = n_all
+        if args.data:
+            np.savez(args.data, X=X, R=R.astype(np.float32), t_solve=t_solve, n_solved=n_solved)
     else:
         X, R, t_solve = make_dataset(range(args.seed0, args.seed0 + n_all), **kw)
         n_solved = n_all
