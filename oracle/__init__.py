@@ -22,6 +22,8 @@ Parity status per function (what pins it; the pins live in ``tests/test_oracle_p
   rk4          the RK4 stability polynomial applied to the extracted generator
   insert       analytic derivative of the Boltzmann distribution; zero total mass
   observe      Gaussian moments of the sampled Boltzmann distribution
+  residual     zero on an exact null vector of the extracted generator, invariance under scaling,
+               sixth-order decay on the sampled Boltzmann state
   equilibrate  stationarity of its result; agreement with the sampled Boltzmann to O(h^6)
   response1/2  closed forms and moment closure above
   response3    the moment closure (one mode, deep hierarchy, linear and quadratic optics) and

@@ -527,3 +527,30 @@ def test_equilibrate_reaches_discrete_steady_state():
     G, steps, r = oracle.equilibrate(pb, wl.dt, 3000, 1e-9, 100)
     assert r < r0 / 20
     assert np.abs(G - G_B).max() < 1e-3 * np.abs(G_B).max()
+
+
+def test_residual_pins():
+    """orc_residual (max |M g| / max |g|, the equilibration's stop criterion, Sec. IV B): zero on
+    an exact null vector of the generator (extracted column by column and solved for with numpy),
+    invariant under scaling and sign, and O(h^6) on the sampled Boltzmann state (the ratio between
+    two resolutions close to the ratio of h^6)."""
+    model = inputs.Model(nmodes=1, kT=0.8, m=(1.1,), omega=(0.9,), g4=(0.05,), zeta=(0.3,),
+                         gamma=(1.2,), V_LL=(1.0,), V_SL=(0.2,))
+    grid = inputs.default_grid(model, [9])
+    pb = oracle.Problem(model, grid, 2)
+    N = pb.M * pb.P
+    M = np.stack([oracle.rhs(pb, np.eye(N)[j].reshape(pb.state_shape)).ravel() for j in range(N)], axis=1)
+    w, V = np.linalg.eig(M)
+    j = int(np.argmin(np.abs(w)))
+    assert abs(w[j]) < 1e-10                       # the generator has a null vector (stationary state)
+    v = np.real(V[:, j] * np.exp(-1j * np.angle(V[np.argmax(np.abs(V[:, j])), j])))
+    assert oracle.residual(pb, v.reshape(pb.state_shape)) < 1e-10
+    W = inputs.random_state(grid, pb.M, seed=3, smooth=True)
+    r = oracle.residual(pb, W)
+    assert r > 1e-3
+    assert oracle.residual(pb, -3.7 * W) == pytest.approx(r, rel=1e-14)
+    res = []
+    for n in (64, 96):   # a domain wide enough (U = 32 kT, 8 sigma in p) that the ends do not show
+        pbn = oracle.Problem(model, inputs.default_grid(model, [n], cut=32.0, nsigma=8.0), 2)
+        res.append(oracle.residual(pbn, oracle.boltzmann(pbn)))
+    assert 0.7 * (96 / 64) ** 6 < res[0] / res[1] < 1.4 * (96 / 64) ** 6, res
