@@ -5,6 +5,7 @@
 #include "kernels.cuh"
 #include "stage_launch.cuh"
 #include "hermite.cuh"
+#include "batch_persistent.cuh"
 #include "persistent.cuh"
 
 #include <cuda_runtime.h>
@@ -132,6 +133,8 @@ struct chfpe_handle {
     // nominal step with j % (nsub / nsub_i) == 0; level l holds the instances whose period
     // nsub / nsub_i divides 2^l (level log2(nsub) = every instance)
     std::vector<int2 *> lv_ptr;         // [level * 3 + list]
+    int2 **d_lv_lists = nullptr;        // device copies of lv_ptr and lv_n (persistent batch kernel)
+    int *d_lv_counts = nullptr;
     std::vector<int> lv_n;
     std::vector<double> lv_bytes, lv_cells;
     int nlevels = 0;
@@ -308,7 +311,7 @@ static chfpe_status check_device_error(chfpe_handle *h) {
     CK(cudaStreamSynchronize(h->stream));
     if (v) {
         CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
-        return fail(CHFPE_ETIMEOUT, "a bounded wait of the bulk-copy stage kernel gave up");
+        return fail(CHFPE_ETIMEOUT, "a bounded wait (grid barrier or bulk copy) gave up");
     }
     return CHFPE_OK;
 }
@@ -721,7 +724,8 @@ extern "C" void chfpe_destroy(chfpe_handle *h) {
     if (h->borrowed_arenas) h->cy = h->ca = h->cb = h->eq = nullptr;
     void *ptrs[] = {h->U_d, h->F_d, h->F_f, h->wp, h->CWq, h->np_d, h->plo_d, h->ph_d, h->inv2m_d,
                     h->cy, h->ca, h->cb, h->by, h->ba, h->bb, h->eq, h->stage64, h->partial, h->dR,
-                    h->counter, h->d_err, h->d_bar, h->d_geo, h->dq, h->pcr, h->pcr32};
+                    h->counter, h->d_err, h->d_bar, h->d_geo, h->dq, h->pcr, h->pcr32,
+                    h->d_lv_lists, h->d_lv_counts};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->lv_ptr.empty()) {            // work lists still owned by d_work (set-up failed)
@@ -1736,10 +1740,90 @@ static void use_level(chfpe_handle *b, int l) {
 // nslots substep slots (a nominal step of dt is nsub slots; calls start on a nominal step): slot
 // j runs the instances of level (j == 0 ? log2(nsub) : number of trailing zero bits of j), each
 // with its own stage coefficients
+// ------------------------------------------------------------------------------------------
+// persistent batch propagation (batch_persistent.cuh): the substep slots of a batch of small
+// instances in one cooperative launch
+// ------------------------------------------------------------------------------------------
+
+constexpr double kBatchPersistCells = 4.0e6;   // batch cells up to which the persistent path may run
+
+template <typename T, int D, int DEPTH, int M32>
+static chfpe_status launch_batch_persistent(chfpe_handle *b, BatchPersistArgs<T> p) {
+    constexpr bool FOUR = tunable(sizeof(T), D, DEPTH);
+    auto kern = batch_persistent_kernel<T, D, DEPTH, M32, kVec, FOUR>;
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return fail(CHFPE_ECUDA, "cooperative launch not supported");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0));
+    int items = 1;   // the most items of one (level, class) list bounds the useful grid
+    for (size_t k = 0; k < b->lv_n.size(); ++k) items = std::max(items, b->lv_n[k]);
+    const long long grid = std::min<long long>(items, (long long)per_sm * sms);
+    if (grid < 1) return fail(CHFPE_EINVAL, "persistent batch: no co-resident blocks");
+    CK(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->stream));
+    {   // test hook: the error word set before the launch, as if a wait had given up
+        const char *ef = getenv("CHFPE_TEST_PRESET_ERROR");
+        if (ef && ef[0] == '1') {
+            const int one = 1;
+            CK(cudaMemcpyAsync(b->d_err, &one, sizeof one, cudaMemcpyHostToDevice, b->stream));
+        }
+    }
+    void *args[] = {&p};
+    CK(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid), dim3(128), args, 0, b->stream));
+    ++b->launches;
+    return CHFPE_OK;
+}
+
+static bool batch_persistent_config(int d, int depth) {
+    return (d == 1 && depth == 5) || (d == 2 && (depth == 2 || depth == 4));
+}
+
+static bool batch_persistent_ok(chfpe_handle *b) {
+    if (!b->use_persistent || b->time_stages || !b->d_bar || !b->d_lv_lists || b->M32 != b->M ||
+        !batch_persistent_config(b->d, b->depth) || b->cells_total > kBatchPersistCells)
+        return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(b->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+template <typename T>
+static chfpe_status batch_persistent(chfpe_handle *b, long nslots) {
+    BatchPersistArgs<T> p;
+    memset(&p, 0, sizeof(p));
+    p.inst = (const InstGeo<T> *)b->d_geo;
+    p.lists = b->d_lv_lists;
+    p.counts = b->d_lv_counts;
+    p.y = (char *)b->cy;
+    p.za = (char *)b->ca;
+    p.zb = (char *)b->cb;
+    p.nslots = nslots;
+    p.nsub = b->nsub;
+    p.top = b->nlevels - 1;
+    p.bar = b->d_bar;
+    p.err = b->d_err;
+    chfpe_status st = fail(CHFPE_EINVAL, "persistent batch: configuration not compiled");
+    if (b->d == 1 && b->depth == 5) st = launch_batch_persistent<T, 1, 5, member_count(1, 5)>(b, p);
+    else if (b->d == 2 && b->depth == 2) st = launch_batch_persistent<T, 2, 2, member_count(2, 2)>(b, p);
+    else if (b->d == 2 && b->depth == 4) st = launch_batch_persistent<T, 2, 4, member_count(2, 4)>(b, p);
+    if (st) return st;
+    const long top = b->nlevels - 1;
+    for (long k = 0; k < nslots; ++k) {   // the cells the slots advance, as batch_rk4 counts them
+        const long j = k % b->nsub;
+        b->cell_updates += b->lv_cells[j == 0 ? top : __builtin_ctzl((unsigned long)j)];
+    }
+    return CHFPE_OK;
+}
+
 template <typename T>
 static chfpe_status batch_rk4(chfpe_handle *b, long nslots) {
     chfpe_status st;
     if (nslots <= 0) return CHFPE_OK;
+    if (batch_persistent_ok(b)) return batch_persistent<T>(b, nslots);
     const int top = b->nlevels - 1;
     if (b->time_stages && (st = burst_event(b))) return st;
     for (long k = 0; k < nslots; ++k) {
@@ -1889,6 +1973,14 @@ static chfpe_status batch_setup_geo(chfpe_handle *b) {
             }
     }
     use_level(b, top);
+    // the level lists as device arrays for the persistent batch kernel
+    b->d_lv_lists = dalloc<int2 *>(b->lv_ptr.size(), &st);
+    if (!st) b->d_lv_counts = dalloc<int>(b->lv_n.size(), &st);
+    if (st) return st;
+    CK(cudaMemcpyAsync(b->d_lv_lists, b->lv_ptr.data(), b->lv_ptr.size() * sizeof(int2 *),
+                       cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->d_lv_counts, b->lv_n.data(), b->lv_n.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, b->stream));
     CK(cudaStreamSynchronize(b->stream));
     return CHFPE_OK;
 }
@@ -1953,6 +2045,17 @@ extern "C" chfpe_status chfpe_create_batch(int n, const chfpe_model *models, con
     b->partial_cap = 4096;
     if (!st) b->partial = dalloc<double>(b->partial_cap, &st);
     if (!st) b->counter = dalloc<int>(1, &st);
+    if (!st) b->d_bar = dalloc<unsigned>(2, &st);
+    if (!st) b->d_err = dalloc<int>(1, &st);
+    if (!st && cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream) != cudaSuccess)
+        st = fail(CHFPE_ECUDA, "error word");
+    {   // the persistent batch path is measured slower than CUDA-graph sampling intervals on
+        // batches of small instances (the stage kernels already dominate there): opt-in
+        const char *ep = getenv("CHFPE_BATCH_PERSISTENT");
+        b->use_persistent = ep && ep[0] == '1' ? 1 : 0;
+        const char *eg = getenv("CHFPE_GRAPHS");
+        if (eg) b->use_graphs = atoi(eg);
+    }
     void **arenas[] = {&b->cy, &b->ca, &b->cb, &b->eq};
     for (void **p : arenas) if (!st) *p = (void *)dalloc<char>((size_t)total, &st);
     if (st) { chfpe_destroy(b); return st; }
@@ -2022,8 +2125,9 @@ extern "C" chfpe_status chfpe_batch_response1(chfpe_handle *b, const chfpe_optic
         return b->prec == 64 ? batch_rk4<double>(b, steps) : batch_rk4<float>(b, steps);
     };
     if ((st = observe_all(0, nullptr))) return st;
+    // small batches: one persistent launch per sampling interval instead of a graph of launches
     const bool graphs = b->use_graphs != 0 && nt > 2 && steps > 0 && !b->time_stages &&
-                        b->cells_total * 4.0 * steps < 2e9;
+                        b->cells_total * 4.0 * steps < 2e9 && !batch_persistent_ok(b);
     if (!graphs) {
         for (int k = 1; k < nt; ++k) {
             if ((st = advance())) return st;
@@ -2114,6 +2218,10 @@ static chfpe_status build_branches(chfpe_handle *b, int cap) {
     void **arenas[] = {&bb->cy, &bb->ca, &bb->cb};
     for (void **p : arenas) if (!st) *p = (void *)dalloc<char>((size_t)total, &st);
     if (!st) CK(cudaMemsetAsync(bb->cy, 0, (size_t)total, bb->stream));
+    bb->use_persistent = b->use_persistent;
+    if (!st) bb->d_bar = dalloc<unsigned>(2, &st);
+    if (!st) bb->d_err = dalloc<int>(1, &st);
+    if (!st) CK(cudaMemsetAsync(bb->d_err, 0, sizeof(int), bb->stream));
     for (int i = 0; i < n && !st; ++i)
         st = ensure_partial(b->inst[i], observe_blocks(b->inst[i]) * cap);
     if (!st) st = b->prec == 64 ? batch_setup_geo<double>(bb) : batch_setup_geo<float>(bb);
@@ -2175,5 +2283,7 @@ extern "C" chfpe_status chfpe_batch_response2(chfpe_handle *b, const chfpe_optic
     b->cell_updates += bb->cell_updates - cells0;
     b->launches += bb->launches - launches0;
     for (int i = 0; i < n; ++i) b->inst[i]->have_state = true;
+    CK(cudaStreamSynchronize(b->stream));
+    if ((st = check_device_error(bb))) return st;   // the branch batch's bounded waits
     return finish_response(b, R, (size_t)n * per);
 }

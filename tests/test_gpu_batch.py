@@ -336,3 +336,56 @@ def test_batch_rows_of_any_length_match_single_handles_and_oracle(tier):
             pb = oracle.Problem(m, g, depth)
             want = oracle.response1(pb, mu, mu, W.astype(np.float32).astype(np.float64), dt, nt, stride)
             assert np.abs(R[i] - want).max() <= 1e-4 * np.abs(want).max(), grids[i]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_persistent_batch_matches_launch_per_stage(prec, monkeypatch):
+    """A batch of small uneven instances (with a stiff one, which may substep) advances its
+    substep slots in one cooperative launch per sampling interval (CHFPE_BATCH_PERSISTENT=1): R1
+    and R2 equal the launch-per-stage path to rounding, with far fewer launches."""
+    chfpe = _chfpe()
+    insts = _instances()
+    stiff = inputs.sweep_instance(110)              # needs dt / 2
+    insts.append((stiff.model, inputs.default_grid(stiff.model, [10, 11, 12, 10], cut=12.0, nsigma=5.0)))
+    depth, dt, nt, stride = 2, 0.006, 5, 6
+    mu = inputs.Optical(lin=(1.0, 1.0), quad=[[0.2, 0.0], [0.0, -0.1]])
+    out = {}
+    monkeypatch.setenv("CHFPE_GRAPHS", "0")            # the other path: one launch per stage
+    for mode in ("1", "0"):
+        monkeypatch.setenv("CHFPE_BATCH_PERSISTENT", mode)
+        with chfpe.Batch([m for m, _ in insts], [g for _, g in insts], depth=depth, dt=dt,
+                         precision=prec, max_batch=3) as b:
+            for i, (m, g) in enumerate(insts):
+                b.instance(i).set_equilibrium(_eq(m, g, depth))
+            b.stats_reset()
+            r1 = b.response1_all(mu, mu, nt, stride)
+            launches = b.stats()["kernel_launches"]
+            r2 = b.response2_all(mu, mu, mu, 3, 3, stride)
+        out[mode] = (r1, r2, launches)
+    tol = 1e-13 if prec == 64 else 1e-6
+    for k in (0, 1):
+        scale = np.abs(out["0"][k]).max()
+        assert np.abs(out["1"][k] - out["0"][k]).max() <= tol * scale, k
+    assert out["1"][2] < out["0"][2] / 4, (out["1"][2], out["0"][2])
+
+
+def test_persistent_batch_barrier_error_reports_timeout_and_recovers(monkeypatch):
+    """The error word set before the launch (as if a grid-barrier wait had given up): every block
+    leaves at its first barrier, the call returns CHFPE_ETIMEOUT, and the next call is exact."""
+    chfpe = _chfpe()
+    monkeypatch.setenv("CHFPE_BATCH_PERSISTENT", "1")
+    insts = _instances()
+    depth, dt, nt, stride = 2, 0.004, 4, 5
+    mu = inputs.Optical(lin=(1.0, 1.0))
+    with chfpe.Batch([m for m, _ in insts], [g for _, g in insts], depth=depth, dt=dt,
+                     precision=64) as b:
+        for i, (m, g) in enumerate(insts):
+            b.instance(i).set_equilibrium(_eq(m, g, depth))
+        want = b.response1_all(mu, mu, nt, stride)
+        monkeypatch.setenv("CHFPE_TEST_PRESET_ERROR", "1")
+        with pytest.raises(chfpe.ChfpeError) as e:
+            b.response1_all(mu, mu, nt, stride)
+        assert e.value.status == chfpe.ETIMEOUT
+        monkeypatch.delenv("CHFPE_TEST_PRESET_ERROR")
+        again = b.response1_all(mu, mu, nt, stride)
+    np.testing.assert_array_equal(again, want)
