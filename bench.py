@@ -564,10 +564,18 @@ def run_profile_case(args):
     from paper_2509_25840_b300 import chfpe
     if args.variant is not None:
         os.environ["CHFPE_STAGE_VARIANT"] = str(args.variant)
-    wl = {"two_mode_32": inputs.two_mode_32, "one_mode_64": inputs.one_mode_64,
-          "three_mode_20": inputs.three_mode_20}[args.workload]()
-    h = chfpe.Handle(wl.model, wl.grid, depth=wl.depth, dt=wl.dt, precision=args.precision,
-                     max_batch=args.batch)
+    if args.workload == "two_mode_hermite":
+        wl = inputs.two_mode_32()
+        K = args.hermite_k
+        grid = inputs.Grid(nq=wl.grid.nq, np=(K, K), qmin=wl.grid.qmin, qmax=wl.grid.qmax,
+                           pmin=(0.0, 0.0), pmax=(1.0, 1.0))
+        h = chfpe.Handle(wl.model, grid, depth=wl.depth, dt=wl.dt, precision=args.precision,
+                         max_batch=args.batch, p_basis=1, q_scheme=args.q_scheme)
+    else:
+        wl = {"two_mode_32": inputs.two_mode_32, "one_mode_64": inputs.one_mode_64,
+              "three_mode_20": inputs.three_mode_20}[args.workload]()
+        h = chfpe.Handle(wl.model, wl.grid, depth=wl.depth, dt=wl.dt, precision=args.precision,
+                         max_batch=args.batch)
     dtype = torch.float32 if args.precision == 32 else torch.float64
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.rand((args.batch,) + h.state_shape, dtype=dtype, device="cuda", generator=g) * 1e-3

@@ -846,6 +846,11 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
     void **barenas[] = {&h->by, &h->ba, &h->bb};
     for (void **p : barenas)
         if (!st && opts->max_batch > 0) *p = (void *)dalloc<char>(sbytes * opts->max_batch, &st);
+    if (!st && h->basis) {   // the row-marching stage kernels' shared memory (FP64 equilibration too)
+        cudaError_t ce = configure_hstage<double>();
+        if (ce == cudaSuccess && h->prec == 32) ce = configure_hstage<float>();
+        if (ce != cudaSuccess) st = fail(CHFPE_ECUDA, std::string("stage shared memory: ") + cudaGetErrorString(ce));
+    }
     if (!st && h->qscheme) {
         // max(1, max_batch) states in the handle's precision, and at least one FP64 state (the
         // FP64 equilibration of an FP32 handle runs through the same arrays)

@@ -2,13 +2,101 @@
 // compiled (modes, depth), FP32 and FP64, in a translation unit of their own.
 #include "hermite.cuh"
 
+#include <algorithm>
+#include <cstring>
+
 namespace chfpe {
 
 namespace {
 constexpr int kHNT = 128;
 
+// row-marching kernel (two modes, explicit stencils): shared memory per block (rows long enough
+// that fewer than two blocks fit on an SM run the gather kernel: measured faster there), grid size
+constexpr size_t kRowSmemMax = 112 * 1024;
+constexpr int kRowTargetBlocks = 148 * 8;
+
+template <typename T>
+int row_pad(int KK) {
+    constexpr int W = 16 / sizeof(T);
+    return (3 * KK + W - 1) / W * W;
+}
+
+template <typename T>
+size_t row_smem(long long L, int KK, int n2) {
+    return ((size_t)9 * (size_t)(L + 2 * row_pad<T>(KK)) + (size_t)5 * L + (size_t)14 * n2) * sizeof(T);
+}
+
+template <typename T>
+bool &row_configured() {
+    static bool c = false;
+    return c;
+}
+
+template <typename T, int E>
+cudaError_t configure_row_one() {
+    cudaError_t e = cudaFuncSetAttribute(hstage_row_kernel<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kRowSmemMax);
+    // as much of the unified L1 as shared memory as the blocks need: several blocks per SM
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(hstage_row_kernel<T, E>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+template <typename T>
+cudaError_t configure_row() {
+    if (row_configured<T>()) return cudaSuccess;
+    cudaError_t e = configure_row_one<T, 1>();
+    if (e == cudaSuccess) e = configure_row_one<T, 2>();
+    if (e == cudaSuccess) e = configure_row_one<T, 3>();
+    if (e == cudaSuccess) e = configure_row_one<T, 4>();
+    if (e == cudaSuccess) e = configure_row_one<T, 5>();
+    if (e == cudaSuccess) e = configure_row_one<T, 6>();
+    if (e == cudaSuccess) e = configure_row_one<T, 7>();
+    if (e == cudaSuccess) e = configure_row_one<T, 8>();
+    if (e == cudaSuccess) row_configured<T>() = true;
+    return e;
+}
+
+template <typename T, int K>
+bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
+    constexpr MemberTable<2, K> tab{};
+    constexpr int M = MemberTable<2, K>::M;
+    static_assert(M <= kRowMaxM, "member table of the row kernel");
+    const int n1 = a.g.n[0], n2 = a.g.n[1], KK = a.g.n[2] * a.g.n[3];
+    const long long L = (long long)n2 * KK;
+    const int E = (int)((L + kRowThreads - 1) / kRowThreads);
+    if (a.dq || E > 8 || row_smem<T>(L, KK, n2) > kRowSmemMax || !row_configured<T>()) return false;
+    const int per = M * batch;
+    const int chunks = std::max(1, std::min(n1 / 4, (kRowTargetBlocks + per - 1) / per));
+    HRowArgs<T> ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.s = a;
+    ra.rows = (n1 + chunks - 1) / chunks;
+    ra.pad = row_pad<T>(KK);
+    ra.vec = ((L * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)a.in & 15) == 0 &&
+              (a.state_bytes & 15) == 0 && ((long long)a.g.P * (long long)sizeof(T)) % 16 == 0) ? 1 : 0;
+    for (int m = 0; m < M; ++m)
+        for (int f = 0; f < 2; ++f) {
+            ra.mt[m][f] = tab.n[m][f];
+            ra.mt[m][2 + f] = tab.up[m][f];
+            ra.mt[m][4 + f] = tab.dn[m][f];
+        }
+    const size_t smem = row_smem<T>(L, KK, n2);
+    const dim3 grid(M, (n1 + ra.rows - 1) / ra.rows, batch);
+    switch (E) {
+#define RCASE(E_) case E_: hstage_row_kernel<T, E_><<<grid, kRowThreads, smem, s>>>(ra); break;
+        RCASE(1) RCASE(2) RCASE(3) RCASE(4) RCASE(5) RCASE(6) RCASE(7) RCASE(8)
+#undef RCASE
+    }
+    return true;
+}
+
 template <typename T, int D, int K>
 void launch_one(const HStageArgs<T> &a, int batch, cudaStream_t s) {
+    if constexpr (D == 2 && K <= 5) {
+        if (launch_row<T, K>(a, batch, s)) return;
+    }
     const dim3 grid((a.g.P + kHNT - 1) / kHNT, batch);
     if (a.dq)
         hstage_kernel<T, D, K, kHNT, true><<<grid, kHNT, 0, s>>>(a);
@@ -71,6 +159,12 @@ template <>
 bool launch_hstage<double>(int d, int depth, const HStageArgs<double> &a, int batch, cudaStream_t s) {
     return launch_any<double>(d, depth, a, batch, s);
 }
+
+template <>
+cudaError_t configure_hstage<float>() { return configure_row<float>(); }
+
+template <>
+cudaError_t configure_hstage<double>() { return configure_row<double>(); }
 
 template <>
 cudaError_t configure_hderiv<float>(int n) { return configure_deriv<float>(n); }

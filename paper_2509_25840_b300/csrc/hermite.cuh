@@ -232,6 +232,176 @@ __global__ void __launch_bounds__(NT) hstage_kernel(const HStageArgs<T> a) {
     }
 }
 
+// The same stage for two modes with explicit q stencils, one block per (state, member, chunk of
+// q_1 rows), marching along q_1.  A q_1 row (every q_2 and k of one q_1 value, L = n_2 K_1 K_2
+// contiguous values) is the unit: a ring of 7 rows in shared memory holds the q_1 stencil's
+// window, filled by asynchronous copies one row ahead (rows outside the grid are zeros), so each
+// row is read from global memory once per chunk plus the chunk's 6 halo rows.  Every ring row is
+// padded with zeros along q_2 (3 K_1 K_2 values each side), so the q_2 taps need no test.  Per
+// row, phase 1 forms every element's q-derivative sums D_1 c, D_2 c into shared memory while the
+// row's base values y and the four hierarchy-link rows (the neighbour members, same row) arrive
+// by asynchronous copies; phase 2 forms, with F_s and the centre values of the same q point,
+//   dc_k/dt = -gamma c_k + sum_s [ sqrt(k_s+1) A_s(k+e_s) - sqrt(k_s) B_s(k-e_s) ] + links,
+//   A_s = F_s c - cq_s D_s c,   B_s = F_s c + cq_s D_s c,
+// and stores y + c * (dc/dt).  Thread t owns the row positions t + j kRowThreads (j < E) in
+// every row, their ladder factors (zero where k -+ e_s leaves the basis) kept in registers.
+// Equal to hstage_kernel up to the order of the additions.
+constexpr int kRowThreads = 256, kRowMaxM = 21;
+
+template <typename T>
+struct HRowArgs {
+    HStageArgs<T> s;
+    int rows;                    // q_1 rows per chunk
+    int vec;                     // 1: rows start on 16-byte boundaries (16-byte copies)
+    int pad;                     // zeros on each side of a ring row (>= 3 K_1 K_2, 16-byte multiple)
+    int mt[kRowMaxM][6];         // per member: n_1, n_2, up_1, up_2, dn_1, dn_2 (-1: none)
+};
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// n values global -> shared, asynchronous, by the whole block (vec: 16-byte copies)
+template <typename T>
+__device__ __forceinline__ void hrow_copy(T *dst, const T *src, int n, bool vec) {
+    if (vec) {
+        constexpr int W = 16 / sizeof(T);
+        for (int x = threadIdx.x * W; x < n; x += kRowThreads * W) cp_async16(dst + x, src + x, 16);
+    } else {
+        for (int x = threadIdx.x; x < n; x += kRowThreads) cp_async_elem(dst + x, src + x);
+    }
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(kRowThreads, 3) hstage_row_kernel(const HRowArgs<T> ra) {
+    const HStageArgs<T> &a = ra.s;
+    const HGeo<T> &g = a.g;
+    extern __shared__ __align__(16) unsigned char hrow_smem[];
+    const int n1 = g.n[0], n2 = g.n[1], K1 = g.n[2], K2 = g.n[3];
+    const int KK = K1 * K2, L = n2 * KK, S = L + 2 * ra.pad;   // row, padded row
+    T *ring = reinterpret_cast<T *>(hrow_smem) + ra.pad;      // 7 padded rows (interiors)
+    T *dd = ring + 7 * S;                                      // D_1 c, D_2 c (padded rows)
+    T *lrow = dd + 2 * S - ra.pad;                             // y, up_1, up_2, dn_1, dn_2 of row i
+    T *fr = lrow + 5 * L;                                      // 7 rows of (F_1, F_2)
+    const int m = blockIdx.x;
+    int mt[6];
+#pragma unroll
+    for (int i = 0; i < kRowMaxM; ++i)
+        if (i == m) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) mt[f] = ra.mt[i][f];
+        }
+    const int r0 = blockIdx.y * ra.rows, r1 = min(n1, r0 + ra.rows);
+    const long long boff = (long long)blockIdx.z * a.state_bytes;
+    const T *in = reinterpret_cast<const T *>(a.in + boff);
+    const T *cm = in + (long long)m * g.P;
+    T *out = reinterpret_cast<T *>(a.out + boff) + (long long)m * g.P;
+    const T *y = a.y ? reinterpret_cast<const T *>(a.y + boff) + (long long)m * g.P : nullptr;
+    const bool vec = ra.vec != 0;
+    // the members of the links (nullptr: none) and their factors
+    const T *lsrc[5] = {y, mt[2] >= 0 ? in + (long long)mt[2] * g.P : nullptr,
+                        mt[3] >= 0 ? in + (long long)mt[3] * g.P : nullptr,
+                        mt[4] >= 0 ? in + (long long)mt[4] * g.P : nullptr,
+                        mt[5] >= 0 ? in + (long long)mt[5] * g.P : nullptr};
+    const T wup0 = mt[2] >= 0 ? g.link[0][mt[0] + 1] * g.lk[0] : T(0);
+    const T wup1 = mt[3] >= 0 ? g.link[1][mt[1] + 1] * g.lk[1] : T(0);
+    const T wdn0 = mt[4] >= 0 ? g.link[0][mt[0]] * g.lk[0] : T(0);
+    const T wdn1 = mt[5] >= 0 ? g.link[1][mt[1]] * g.lk[1] : T(0);
+    // zero padding of the 9 padded rows (never written again); link rows of absent members
+    for (int j = threadIdx.x; j < 9 * 2 * ra.pad; j += kRowThreads) {
+        const int r = j / (2 * ra.pad), o = j - r * 2 * ra.pad;
+        ring[r * S + (o < ra.pad ? o - ra.pad : L + o - ra.pad)] = T(0);
+    }
+#pragma unroll
+    for (int l = 1; l < 5; ++l)
+        if (!lsrc[l])
+            for (int x = threadIdx.x; x < L; x += kRowThreads) lrow[l * L + x] = T(0);
+    // row i of the window into its slot: copied, or zeros outside the grid
+    auto load_row = [&](int i) {
+        const int sl = (i + 7) % 7;
+        T *dst = ring + sl * S;
+        if (i >= 0 && i < n1) {
+            hrow_copy(dst, cm + (long long)i * L, L, vec);
+            for (int x = threadIdx.x; x < n2; x += kRowThreads) {
+                cp_async_elem(fr + sl * 2 * n2 + x, g.Fh + (long long)i * n2 + x);
+                cp_async_elem(fr + sl * 2 * n2 + n2 + x, g.Fh + g.NQ + (long long)i * n2 + x);
+            }
+        } else {
+            for (int x = threadIdx.x; x < L; x += kRowThreads) dst[x] = T(0);
+        }
+    };
+    for (int i = r0 - 3; i <= r0 + 3; ++i) load_row(i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // this thread's positions and their ladder factors
+    int xs[E], q2s[E];
+    T s1a[E], s0a[E], s1b[E], s0b[E], V2[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int x = threadIdx.x + j * kRowThreads;
+        const int xr = x < L ? x : L - 1;
+        const int q2 = xr / KK, kk = xr - q2 * KK, k1 = kk / K2, k2 = kk - k1 * K2;
+        xs[j] = x;
+        q2s[j] = q2;
+        s1a[j] = k1 + 1 < K1 ? sqrt(T(k1 + 1)) : T(0);
+        s0a[j] = sqrt(T(k1));
+        s1b[j] = k2 + 1 < K2 ? sqrt(T(k2 + 1)) : T(0);
+        s0b[j] = sqrt(T(k2));
+        V2[j] = g.VLL[1] + g.VSL[1] * (g.qlo[1] + T(q2) * g.qh[1]);
+    }
+    const T gm = T(mt[0]) * g.gam[0] + T(mt[1]) * g.gam[1];
+    const T cq1 = g.cq[0], cq2 = g.cq[1];
+    for (int i = r0; i < r1; ++i) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        // the row's base values and link rows, in flight during phase 1
+        const long long ro = (long long)i * L;
+#pragma unroll
+        for (int l = 0; l < 5; ++l)
+            if (lsrc[l]) hrow_copy(lrow + l * L, lsrc[l] + ro, L, vec);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // phase 1: D_1 c, D_2 c of every element of row i
+        const T *R0 = ring + (i % 7) * S;
+        {
+            const T *Rp1 = ring + ((i + 1) % 7) * S, *Rp2 = ring + ((i + 2) % 7) * S, *Rp3 = ring + ((i + 3) % 7) * S;
+            const T *Rm1 = ring + ((i + 6) % 7) * S, *Rm2 = ring + ((i + 5) % 7) * S, *Rm3 = ring + ((i + 4) % 7) * S;
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const int x = xs[j];
+                if (j == E - 1 && x >= L) break;
+                dd[x] = T(45) * (Rp1[x] - Rm1[x]) - T(9) * (Rp2[x] - Rm2[x]) + (Rp3[x] - Rm3[x]);
+                dd[S + x] = T(45) * (R0[x + KK] - R0[x - KK]) - T(9) * (R0[x + 2 * KK] - R0[x - 2 * KK]) +
+                            (R0[x + 3 * KK] - R0[x - 3 * KK]);
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        // the next row of the window (its slot held row i - 3), in flight during phase 2
+        if (i + 1 < r1) load_row(i + 4);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // phase 2
+        const T V1 = g.VLL[0] + g.VSL[0] * (g.qlo[0] + T(i) * g.qh[0]);
+        const T ldn0 = wdn0 * V1, lup0 = wup0 * V1;
+        const T *F = fr + (i % 7) * 2 * n2;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int x = xs[j];
+            if (j == E - 1 && x >= L) break;
+            const T F1 = F[q2s[j]], F2 = F[n2 + q2s[j]];
+            T acc = -gm * R0[x];
+            acc += s1a[j] * (F1 * R0[x + K2] - cq1 * dd[x + K2] + ldn0 * lrow[3 * L + min(x + K2, L - 1)]);
+            acc -= s0a[j] * (F1 * R0[x - K2] + cq1 * dd[x - K2] + lup0 * lrow[L + max(x - K2, 0)]);
+            acc += s1b[j] * (F2 * R0[x + 1] - cq2 * dd[S + x + 1] + wdn1 * V2[j] * lrow[4 * L + min(x + 1, L - 1)]);
+            acc -= s0b[j] * (F2 * R0[x - 1] + cq2 * dd[S + x - 1] + wup1 * V2[j] * lrow[2 * L + max(x - 1, 0)]);
+            out[ro + x] = y ? lrow[x] + a.c * acc : a.c * acc;
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename T>
 struct HInsertArgs {
     const char *in;
@@ -300,6 +470,15 @@ template <>
 bool launch_hstage<float>(int d, int depth, const HStageArgs<float> &a, int batch, cudaStream_t s);
 template <>
 bool launch_hstage<double>(int d, int depth, const HStageArgs<double> &a, int batch, cudaStream_t s);
+
+// opts the row-marching stage kernels (hstage_row_kernel) into the shared memory they may use;
+// once per element type, before any launch or stream capture that uses them
+template <typename T>
+cudaError_t configure_hstage();
+template <>
+cudaError_t configure_hstage<float>();
+template <>
+cudaError_t configure_hstage<double>();
 
 // compact derivative along one q axis of `batch` states (hderiv_pcr_kernel); configure_hderiv
 // opts the kernels into the shared memory lines of n points need (once, before any launch or

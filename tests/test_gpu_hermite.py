@@ -58,6 +58,11 @@ CASES = [
     (2, [11, 13], [5, 6], 4),
     (2, [9, 10], [7, 3], 2),
     (3, [7, 8, 9], [3, 4, 2], 2),
+    (2, [11, 13], [6, 6], 5),      # row-marching kernel: 2, 2 and 8 elements per thread
+    (2, [10, 7], [8, 8], 3),
+    (2, [9, 40], [6, 7], 2),
+    (2, [8, 32], [6, 6], 4),       # the 32-point q_2 rows of 6 x 6 functions (5 per thread)
+    (2, [7, 131], [6, 6], 1),      # the shortest q extent; rows too long for it (gather kernel)
 ]
 
 
@@ -90,7 +95,7 @@ def test_hermite_rhs_matches_oracle(d, nq, K, depth, prec):
 
 
 @pytest.mark.parametrize("prec", [64, 32])
-@pytest.mark.parametrize("d,nq,K,depth", [CASES[0], CASES[2], CASES[4]])
+@pytest.mark.parametrize("d,nq,K,depth", [CASES[0], CASES[2], CASES[4], CASES[5], CASES[7], CASES[8]])
 def test_hermite_rk4_insert_observe_match_oracle(d, nq, K, depth, prec):
     model, grid, h, pb = _setup(d, nq, K, depth, prec, max_batch=2)
     with h:
