@@ -22,8 +22,16 @@ int row_pad(int KK) {
 }
 
 template <typename T>
-size_t row_smem(long long L, int KK, int n2) {
-    return ((size_t)9 * (size_t)(L + 2 * row_pad<T>(KK)) + (size_t)5 * L + (size_t)14 * n2) * sizeof(T);
+int row_lpad(int K2) {
+    constexpr int W = 16 / sizeof(T);
+    return (std::max(K2, 2) + W - 1) / W * W;
+}
+
+// shared memory of the scalar (pair = false) and the pair kernel
+template <typename T>
+size_t row_smem(long long L, int KK, int K2, int n2, bool pair) {
+    const long long link = pair ? L + 2 * row_lpad<T>(K2) : L;
+    return ((size_t)9 * (size_t)(L + 2 * row_pad<T>(KK)) + (size_t)5 * link + (size_t)14 * n2) * sizeof(T);
 }
 
 template <typename T>
@@ -32,14 +40,20 @@ bool &row_configured() {
     return c;
 }
 
-template <typename T, int E>
-cudaError_t configure_row_one() {
-    cudaError_t e = cudaFuncSetAttribute(hstage_row_kernel<T, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kRowSmemMax);
+template <typename K>
+cudaError_t configure_kernel(K *k) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmemMax);
     // as much of the unified L1 as shared memory as the blocks need: several blocks per SM
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(hstage_row_kernel<T, E>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+template <typename T, int E>
+cudaError_t configure_row_one() {
+    cudaError_t e = configure_kernel(hstage_row_kernel<T, E>);
+    if (e == cudaSuccess) e = configure_kernel(hstage_row2_kernel<T, E>);
     return e;
 }
 
@@ -63,10 +77,15 @@ bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
     constexpr MemberTable<2, K> tab{};
     constexpr int M = MemberTable<2, K>::M;
     static_assert(M <= kRowMaxM, "member table of the row kernel");
-    const int n1 = a.g.n[0], n2 = a.g.n[1], KK = a.g.n[2] * a.g.n[3];
+    const int n1 = a.g.n[0], n2 = a.g.n[1], K2 = a.g.n[3], KK = a.g.n[2] * K2;
     const long long L = (long long)n2 * KK;
-    const int E = (int)((L + kRowThreads - 1) / kRowThreads);
-    if (a.dq || E > 8 || row_smem<T>(L, KK, n2) > kRowSmemMax || !row_configured<T>()) return false;
+    // element pairs: even K_2, every pair 2-vector aligned
+    const uintptr_t al2 = 2 * sizeof(T) - 1;
+    const bool pair = K2 % 2 == 0 && ((uintptr_t)a.in & al2) == 0 && ((uintptr_t)a.out & al2) == 0 &&
+                      ((uintptr_t)a.y & al2) == 0 && (a.state_bytes & (long long)al2) == 0;
+    const int E = (int)((L + (pair ? 2 : 1) * kRowThreads - 1) / ((pair ? 2 : 1) * kRowThreads));
+    const size_t smem = row_smem<T>(L, KK, K2, n2, pair);
+    if (a.dq || E > 8 || smem > kRowSmemMax || !row_configured<T>()) return false;
     const int per = M * batch;
     const int chunks = std::max(1, std::min(n1 / 4, (kRowTargetBlocks + per - 1) / per));
     HRowArgs<T> ra;
@@ -74,6 +93,7 @@ bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
     ra.s = a;
     ra.rows = (n1 + chunks - 1) / chunks;
     ra.pad = row_pad<T>(KK);
+    ra.lpad = row_lpad<T>(K2);
     ra.vec = ((L * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)a.in & 15) == 0 &&
               (a.state_bytes & 15) == 0 && ((long long)a.g.P * (long long)sizeof(T)) % 16 == 0) ? 1 : 0;
     for (int m = 0; m < M; ++m)
@@ -82,10 +102,11 @@ bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
             ra.mt[m][2 + f] = tab.up[m][f];
             ra.mt[m][4 + f] = tab.dn[m][f];
         }
-    const size_t smem = row_smem<T>(L, KK, n2);
     const dim3 grid(M, (n1 + ra.rows - 1) / ra.rows, batch);
-    switch (E) {
-#define RCASE(E_) case E_: hstage_row_kernel<T, E_><<<grid, kRowThreads, smem, s>>>(ra); break;
+    switch (E * 2 + (pair ? 1 : 0)) {
+#define RCASE(E_)                                                                    \
+    case 2 * E_: hstage_row_kernel<T, E_><<<grid, kRowThreads, smem, s>>>(ra); break; \
+    case 2 * E_ + 1: hstage_row2_kernel<T, E_><<<grid, kRowThreads, smem, s>>>(ra); break;
         RCASE(1) RCASE(2) RCASE(3) RCASE(4) RCASE(5) RCASE(6) RCASE(7) RCASE(8)
 #undef RCASE
     }

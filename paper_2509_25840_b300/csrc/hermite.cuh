@@ -254,6 +254,7 @@ struct HRowArgs {
     int rows;                    // q_1 rows per chunk
     int vec;                     // 1: rows start on 16-byte boundaries (16-byte copies)
     int pad;                     // zeros on each side of a ring row (>= 3 K_1 K_2, 16-byte multiple)
+    int lpad;                    // zeros on each side of a link row (pair kernel: >= K_2, 16-byte multiple)
     int mt[kRowMaxM][6];         // per member: n_1, n_2, up_1, up_2, dn_1, dn_2 (-1: none)
 };
 
@@ -397,6 +398,169 @@ __global__ void __launch_bounds__(kRowThreads, 3) hstage_row_kernel(const HRowAr
             acc += s1b[j] * (F2 * R0[x + 1] - cq2 * dd[S + x + 1] + wdn1 * V2[j] * lrow[4 * L + min(x + 1, L - 1)]);
             acc -= s0b[j] * (F2 * R0[x - 1] + cq2 * dd[S + x - 1] + wup1 * V2[j] * lrow[2 * L + max(x - 1, 0)]);
             out[ro + x] = y ? lrow[x] + a.c * acc : a.c * acc;
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// The row-marching stage for even K_2 with element pairs: thread t owns the pairs (x, x + 1),
+// x = 2 (t + j kRowThreads), of every row (both of one k_1 row and one q point), read and written
+// as 2-vectors; the link and base rows carry zero pads of >= K_2 values each side, so no
+// neighbour index needs a clamp.  Same phases and shared memory as hstage_row_kernel.
+template <typename T>
+__device__ __forceinline__ typename VecOf<T, 2>::type ld2(const T *p) {
+    return *reinterpret_cast<const typename VecOf<T, 2>::type *>(p);
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(kRowThreads, 3) hstage_row2_kernel(const HRowArgs<T> ra) {
+    typedef typename VecOf<T, 2>::type T2;
+    const HStageArgs<T> &a = ra.s;
+    const HGeo<T> &g = a.g;
+    extern __shared__ __align__(16) unsigned char hrow_smem[];
+    const int n1 = g.n[0], n2 = g.n[1], K1 = g.n[2], K2 = g.n[3];
+    const int KK = K1 * K2, L = n2 * KK, S = L + 2 * ra.pad, SL = L + 2 * ra.lpad;
+    T *ring = reinterpret_cast<T *>(hrow_smem) + ra.pad;      // 7 padded rows (interiors)
+    T *dd = ring + 7 * S;                                      // D_1 c, D_2 c (padded rows)
+    T *lrow = dd + 2 * S - ra.pad + ra.lpad;                   // y, up_1, up_2, dn_1, dn_2 (padded)
+    T *fr = lrow + 5 * SL - ra.lpad;                           // 7 rows of (F_1, F_2)
+    const int m = blockIdx.x;
+    int mt[6];
+#pragma unroll
+    for (int i = 0; i < kRowMaxM; ++i)
+        if (i == m) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) mt[f] = ra.mt[i][f];
+        }
+    const int r0 = blockIdx.y * ra.rows, r1 = min(n1, r0 + ra.rows);
+    const long long boff = (long long)blockIdx.z * a.state_bytes;
+    const T *in = reinterpret_cast<const T *>(a.in + boff);
+    const T *cm = in + (long long)m * g.P;
+    T *out = reinterpret_cast<T *>(a.out + boff) + (long long)m * g.P;
+    const T *y = a.y ? reinterpret_cast<const T *>(a.y + boff) + (long long)m * g.P : nullptr;
+    const bool vec = ra.vec != 0;
+    const T *lsrc[5] = {y, mt[2] >= 0 ? in + (long long)mt[2] * g.P : nullptr,
+                        mt[3] >= 0 ? in + (long long)mt[3] * g.P : nullptr,
+                        mt[4] >= 0 ? in + (long long)mt[4] * g.P : nullptr,
+                        mt[5] >= 0 ? in + (long long)mt[5] * g.P : nullptr};
+    const T wup0 = mt[2] >= 0 ? g.link[0][mt[0] + 1] * g.lk[0] : T(0);
+    const T wup1 = mt[3] >= 0 ? g.link[1][mt[1] + 1] * g.lk[1] : T(0);
+    const T wdn0 = mt[4] >= 0 ? g.link[0][mt[0]] * g.lk[0] : T(0);
+    const T wdn1 = mt[5] >= 0 ? g.link[1][mt[1]] * g.lk[1] : T(0);
+    // zero pads (never written again); the link rows of absent members
+    for (int j = threadIdx.x; j < 9 * 2 * ra.pad; j += kRowThreads) {
+        const int r = j / (2 * ra.pad), o = j - r * 2 * ra.pad;
+        ring[r * S + (o < ra.pad ? o - ra.pad : L + o - ra.pad)] = T(0);
+    }
+    for (int j = threadIdx.x; j < 5 * 2 * ra.lpad; j += kRowThreads) {
+        const int r = j / (2 * ra.lpad), o = j - r * 2 * ra.lpad;
+        lrow[r * SL + (o < ra.lpad ? o - ra.lpad : L + o - ra.lpad)] = T(0);
+    }
+#pragma unroll
+    for (int l = 1; l < 5; ++l)
+        if (!lsrc[l])
+            for (int x = threadIdx.x; x < L; x += kRowThreads) lrow[l * SL + x] = T(0);
+    auto load_row = [&](int i) {
+        const int sl = (i + 7) % 7;
+        T *dst = ring + sl * S;
+        if (i >= 0 && i < n1) {
+            hrow_copy(dst, cm + (long long)i * L, L, vec);
+            for (int x = threadIdx.x; x < n2; x += kRowThreads) {
+                cp_async_elem(fr + sl * 2 * n2 + x, g.Fh + (long long)i * n2 + x);
+                cp_async_elem(fr + sl * 2 * n2 + n2 + x, g.Fh + g.NQ + (long long)i * n2 + x);
+            }
+        } else {
+            for (int x = threadIdx.x; x < L; x += kRowThreads) dst[x] = T(0);
+        }
+    };
+    for (int i = r0 - 3; i <= r0 + 3; ++i) load_row(i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // this thread's pairs: k_1 and q_2 shared, k_2 = kb and kb + 1 (kb even)
+    int xs[E], q2s[E];
+    T s1a[E], s0a[E], s1b0[E], s0b0[E], s1b1[E], s0b1[E], V2[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int x = 2 * (threadIdx.x + j * kRowThreads);
+        const int xr = x < L ? x : L - 2;
+        const int q2 = xr / KK, kk = xr - q2 * KK, k1 = kk / K2, kb = kk - k1 * K2;
+        xs[j] = x;
+        q2s[j] = q2;
+        s1a[j] = k1 + 1 < K1 ? sqrt(T(k1 + 1)) : T(0);
+        s0a[j] = sqrt(T(k1));
+        s1b0[j] = sqrt(T(kb + 1));
+        s0b0[j] = sqrt(T(kb));
+        s1b1[j] = kb + 2 < K2 ? sqrt(T(kb + 2)) : T(0);
+        s0b1[j] = sqrt(T(kb + 1));
+        V2[j] = g.VLL[1] + g.VSL[1] * (g.qlo[1] + T(q2) * g.qh[1]);
+    }
+    const T gm = T(mt[0]) * g.gam[0] + T(mt[1]) * g.gam[1];
+    const T cq1 = g.cq[0], cq2 = g.cq[1];
+    for (int i = r0; i < r1; ++i) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        const long long ro = (long long)i * L;
+#pragma unroll
+        for (int l = 0; l < 5; ++l)
+            if (lsrc[l]) hrow_copy(lrow + l * SL, lsrc[l] + ro, L, vec);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // phase 1: D_1 c, D_2 c of every pair of row i
+        const T *R0 = ring + (i % 7) * S;
+        {
+            const T *Rp1 = ring + ((i + 1) % 7) * S, *Rp2 = ring + ((i + 2) % 7) * S, *Rp3 = ring + ((i + 3) % 7) * S;
+            const T *Rm1 = ring + ((i + 6) % 7) * S, *Rm2 = ring + ((i + 5) % 7) * S, *Rm3 = ring + ((i + 4) % 7) * S;
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const int x = xs[j];
+                if (j == E - 1 && x >= L) break;
+                const T2 p1 = ld2(Rp1 + x), m1 = ld2(Rm1 + x), p2 = ld2(Rp2 + x), m2 = ld2(Rm2 + x);
+                const T2 p3 = ld2(Rp3 + x), m3 = ld2(Rm3 + x);
+                const T2 u1 = ld2(R0 + x + KK), v1 = ld2(R0 + x - KK), u2 = ld2(R0 + x + 2 * KK);
+                const T2 v2 = ld2(R0 + x - 2 * KK), u3 = ld2(R0 + x + 3 * KK), v3 = ld2(R0 + x - 3 * KK);
+                T2 d1, d2;
+                d1.x = T(45) * (p1.x - m1.x) - T(9) * (p2.x - m2.x) + (p3.x - m3.x);
+                d1.y = T(45) * (p1.y - m1.y) - T(9) * (p2.y - m2.y) + (p3.y - m3.y);
+                d2.x = T(45) * (u1.x - v1.x) - T(9) * (u2.x - v2.x) + (u3.x - v3.x);
+                d2.y = T(45) * (u1.y - v1.y) - T(9) * (u2.y - v2.y) + (u3.y - v3.y);
+                *reinterpret_cast<T2 *>(dd + x) = d1;
+                *reinterpret_cast<T2 *>(dd + S + x) = d2;
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        if (i + 1 < r1) load_row(i + 4);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // phase 2
+        const T V1 = g.VLL[0] + g.VSL[0] * (g.qlo[0] + T(i) * g.qh[0]);
+        const T ldn0 = wdn0 * V1, lup0 = wup0 * V1;
+        const T *F = fr + (i % 7) * 2 * n2;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int x = xs[j];
+            if (j == E - 1 && x >= L) break;
+            const T F1 = F[q2s[j]], F2 = F[n2 + q2s[j]];
+            const T ldn1 = wdn1 * V2[j], lup1 = wup1 * V2[j];
+            const T2 c = ld2(R0 + x), cL = ld2(R0 + x - 2), cR = ld2(R0 + x + 2);
+            const T2 cU = ld2(R0 + x + K2), cD = ld2(R0 + x - K2);
+            const T2 e1U = ld2(dd + x + K2), e1D = ld2(dd + x - K2);
+            const T2 e2L = ld2(dd + S + x - 2), e2C = ld2(dd + S + x), e2R = ld2(dd + S + x + 2);
+            const T2 up0 = ld2(lrow + SL + x - K2), dn0 = ld2(lrow + 3 * SL + x + K2);
+            const T2 up1L = ld2(lrow + 2 * SL + x - 2), up1C = ld2(lrow + 2 * SL + x);
+            const T2 dn1C = ld2(lrow + 4 * SL + x), dn1R = ld2(lrow + 4 * SL + x + 2);
+            T acc0 = -gm * c.x, acc1 = -gm * c.y;
+            acc0 += s1a[j] * (F1 * cU.x - cq1 * e1U.x + ldn0 * dn0.x) - s0a[j] * (F1 * cD.x + cq1 * e1D.x + lup0 * up0.x);
+            acc1 += s1a[j] * (F1 * cU.y - cq1 * e1U.y + ldn0 * dn0.y) - s0a[j] * (F1 * cD.y + cq1 * e1D.y + lup0 * up0.y);
+            acc0 += s1b0[j] * (F2 * c.y - cq2 * e2C.y + ldn1 * dn1C.y) - s0b0[j] * (F2 * cL.y + cq2 * e2L.y + lup1 * up1L.y);
+            acc1 += s1b1[j] * (F2 * cR.x - cq2 * e2R.x + ldn1 * dn1R.x) - s0b1[j] * (F2 * c.x + cq2 * e2C.x + lup1 * up1C.x);
+            T2 r;
+            if (y) {
+                const T2 yv = ld2(lrow + x);
+                r.x = yv.x + a.c * acc0;
+                r.y = yv.y + a.c * acc1;
+            } else {
+                r.x = a.c * acc0;
+                r.y = a.c * acc1;
+            }
+            *reinterpret_cast<T2 *>(out + ro + x) = r;
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
