@@ -54,7 +54,14 @@ template <typename T, int E>
 cudaError_t configure_row_one() {
     cudaError_t e = configure_kernel(hstage_row_kernel<T, E>);
     if (e == cudaSuccess) e = configure_kernel(hstage_row2_kernel<T, E>);
+    if (e == cudaSuccess) e = configure_kernel(hstage_rowpre_kernel<T, E>);
     return e;
+}
+
+// shared memory of the compact-derivative row kernel: 2 x 8 padded rows, 2 x (F_1, F_2)
+template <typename T>
+size_t rowpre_smem(long long L, int K2, int n2) {
+    return ((size_t)16 * (size_t)(L + 2 * row_lpad<T>(K2)) + (size_t)4 * n2) * sizeof(T);
 }
 
 template <typename T>
@@ -84,10 +91,14 @@ bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
     const bool pair = K2 % 2 == 0 && ((uintptr_t)a.in & al2) == 0 && ((uintptr_t)a.out & al2) == 0 &&
                       ((uintptr_t)a.y & al2) == 0 && (a.state_bytes & (long long)al2) == 0;
     const int E = (int)((L + (pair ? 2 : 1) * kRowThreads - 1) / ((pair ? 2 : 1) * kRowThreads));
-    const size_t smem = row_smem<T>(L, KK, K2, n2, pair);
-    if (a.dq || E > 8 || smem > kRowSmemMax || !row_configured<T>()) return false;
+    // compact derivatives: the pair kernel reading the derivative arrays (aligned like the state)
+    const bool pre = a.dq != nullptr;
+    if (pre && (!pair || ((uintptr_t)a.dq & al2) != 0 || (a.dq_state * (long long)sizeof(T)) % (2 * sizeof(T)) != 0))
+        return false;
+    const size_t smem = pre ? rowpre_smem<T>(L, K2, n2) : row_smem<T>(L, KK, K2, n2, pair);
+    if (E > 8 || smem > kRowSmemMax || !row_configured<T>()) return false;
     const int per = M * batch;
-    const int chunks = std::max(1, std::min(n1 / 4, (kRowTargetBlocks + per - 1) / per));
+    const int chunks = std::max(1, std::min(pre ? n1 : n1 / 4, (kRowTargetBlocks + per - 1) / per));
     HRowArgs<T> ra;
     memset(&ra, 0, sizeof(ra));
     ra.s = a;
@@ -95,7 +106,9 @@ bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
     ra.pad = row_pad<T>(KK);
     ra.lpad = row_lpad<T>(K2);
     ra.vec = ((L * (long long)sizeof(T)) % 16 == 0 && ((uintptr_t)a.in & 15) == 0 &&
-              (a.state_bytes & 15) == 0 && ((long long)a.g.P * (long long)sizeof(T)) % 16 == 0) ? 1 : 0;
+              (a.state_bytes & 15) == 0 && ((long long)a.g.P * (long long)sizeof(T)) % 16 == 0 &&
+              ((uintptr_t)a.y & 15) == 0 &&
+              (!pre || (((uintptr_t)a.dq & 15) == 0 && (a.dq_state * (long long)sizeof(T)) % 16 == 0))) ? 1 : 0;
     for (int m = 0; m < M; ++m)
         for (int f = 0; f < 2; ++f) {
             ra.mt[m][f] = tab.n[m][f];
@@ -103,6 +116,14 @@ bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
             ra.mt[m][4 + f] = tab.dn[m][f];
         }
     const dim3 grid(M, (n1 + ra.rows - 1) / ra.rows, batch);
+    if (pre) {
+        switch (E) {
+#define PCASE(E_) case E_: hstage_rowpre_kernel<T, E_><<<grid, kRowThreads, smem, s>>>(ra); break;
+            PCASE(1) PCASE(2) PCASE(3) PCASE(4) PCASE(5) PCASE(6) PCASE(7) PCASE(8)
+#undef PCASE
+        }
+        return true;
+    }
     switch (E * 2 + (pair ? 1 : 0)) {
 #define RCASE(E_)                                                                    \
     case 2 * E_: hstage_row_kernel<T, E_><<<grid, kRowThreads, smem, s>>>(ra); break; \

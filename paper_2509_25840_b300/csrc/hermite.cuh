@@ -566,6 +566,135 @@ __global__ void __launch_bounds__(kRowThreads, 3) hstage_row2_kernel(const HRowA
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// The row-marching stage for the compact q-derivatives (even K_2, element pairs): D_1 c and D_2 c
+// come from the derivative arrays, so no stencil window is needed.  Per row, the centre values,
+// both derivative rows, the base values and the four link rows (8 zero-padded rows) and F are
+// copied by cp.async into one of two buffers while the other buffer's row is computed as in
+// phase 2 of hstage_row2_kernel; one block barrier per row.
+template <typename T, int E>
+__global__ void __launch_bounds__(kRowThreads, 3) hstage_rowpre_kernel(const HRowArgs<T> ra) {
+    typedef typename VecOf<T, 2>::type T2;
+    const HStageArgs<T> &a = ra.s;
+    const HGeo<T> &g = a.g;
+    extern __shared__ __align__(16) unsigned char hrow_smem[];
+    const int n1 = g.n[0], n2 = g.n[1], K1 = g.n[2], K2 = g.n[3];
+    const int KK = K1 * K2, L = n2 * KK, SL = L + 2 * ra.lpad;
+    // two buffers of 8 padded rows: c, D_1 c, D_2 c, y, up_1, up_2, dn_1, dn_2; then 2 x (F_1, F_2)
+    T *buf = reinterpret_cast<T *>(hrow_smem) + ra.lpad;
+    T *fr = buf + 16 * SL - ra.lpad;
+    const int m = blockIdx.x;
+    int mt[6];
+#pragma unroll
+    for (int i = 0; i < kRowMaxM; ++i)
+        if (i == m) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) mt[f] = ra.mt[i][f];
+        }
+    const int r0 = blockIdx.y * ra.rows, r1 = min(n1, r0 + ra.rows);
+    const long long boff = (long long)blockIdx.z * a.state_bytes;
+    const T *in = reinterpret_cast<const T *>(a.in + boff);
+    T *out = reinterpret_cast<T *>(a.out + boff) + (long long)m * g.P;
+    const T *y = a.y ? reinterpret_cast<const T *>(a.y + boff) + (long long)m * g.P : nullptr;
+    const T *dq = a.dq + (long long)blockIdx.z * 2 * a.dq_state + (long long)m * g.P;
+    const bool vec = ra.vec != 0;
+    const T *src[8] = {in + (long long)m * g.P, dq, dq + a.dq_state, y,
+                       mt[2] >= 0 ? in + (long long)mt[2] * g.P : nullptr,
+                       mt[3] >= 0 ? in + (long long)mt[3] * g.P : nullptr,
+                       mt[4] >= 0 ? in + (long long)mt[4] * g.P : nullptr,
+                       mt[5] >= 0 ? in + (long long)mt[5] * g.P : nullptr};
+    const T wup0 = mt[2] >= 0 ? g.link[0][mt[0] + 1] * g.lk[0] : T(0);
+    const T wup1 = mt[3] >= 0 ? g.link[1][mt[1] + 1] * g.lk[1] : T(0);
+    const T wdn0 = mt[4] >= 0 ? g.link[0][mt[0]] * g.lk[0] : T(0);
+    const T wdn1 = mt[5] >= 0 ? g.link[1][mt[1]] * g.lk[1] : T(0);
+    // zero pads (never written again); the rows of absent sources in both buffers
+    for (int j = threadIdx.x; j < 16 * 2 * ra.lpad; j += kRowThreads) {
+        const int r = j / (2 * ra.lpad), o = j - r * 2 * ra.lpad;
+        buf[r * SL + (o < ra.lpad ? o - ra.lpad : L + o - ra.lpad)] = T(0);
+    }
+#pragma unroll
+    for (int l = 3; l < 8; ++l)
+        if (!src[l])
+            for (int x = threadIdx.x; x < 2 * L; x += kRowThreads) {
+                const int b = x >= L ? 1 : 0;
+                buf[(b * 8 + l) * SL + x - b * L] = T(0);
+            }
+    auto issue = [&](int i) {
+        const int b = i & 1;
+        const long long ro = (long long)i * L;
+#pragma unroll
+        for (int l = 0; l < 8; ++l)
+            if (src[l]) hrow_copy(buf + (b * 8 + l) * SL, src[l] + ro, L, vec);
+        for (int x = threadIdx.x; x < n2; x += kRowThreads) {
+            cp_async_elem(fr + b * 2 * n2 + x, g.Fh + (long long)i * n2 + x);
+            cp_async_elem(fr + b * 2 * n2 + n2 + x, g.Fh + g.NQ + (long long)i * n2 + x);
+        }
+    };
+    if (r0 < r1) issue(r0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    int xs[E], q2s[E];
+    T s1a[E], s0a[E], s1b0[E], s0b0[E], s1b1[E], s0b1[E], V2[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        const int x = 2 * (threadIdx.x + j * kRowThreads);
+        const int xr = x < L ? x : L - 2;
+        const int q2 = xr / KK, kk = xr - q2 * KK, k1 = kk / K2, kb = kk - k1 * K2;
+        xs[j] = x;
+        q2s[j] = q2;
+        s1a[j] = k1 + 1 < K1 ? sqrt(T(k1 + 1)) : T(0);
+        s0a[j] = sqrt(T(k1));
+        s1b0[j] = sqrt(T(kb + 1));
+        s0b0[j] = sqrt(T(kb));
+        s1b1[j] = kb + 2 < K2 ? sqrt(T(kb + 2)) : T(0);
+        s0b1[j] = sqrt(T(kb + 1));
+        V2[j] = g.VLL[1] + g.VSL[1] * (g.qlo[1] + T(q2) * g.qh[1]);
+    }
+    const T gm = T(mt[0]) * g.gam[0] + T(mt[1]) * g.gam[1];
+    const T cq1 = g.cq[0], cq2 = g.cq[1];
+    for (int i = r0; i < r1; ++i) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        if (i + 1 < r1) issue(i + 1);   // into the buffer the previous row used
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        const int b = i & 1;
+        const T *R0 = buf + (b * 8) * SL, *d1 = R0 + SL, *d2 = R0 + 2 * SL, *yr = R0 + 3 * SL;
+        const T *u0 = R0 + 4 * SL, *u1 = R0 + 5 * SL, *w0 = R0 + 6 * SL, *w1 = R0 + 7 * SL;
+        const T *F = fr + b * 2 * n2;
+        const T V1 = g.VLL[0] + g.VSL[0] * (g.qlo[0] + T(i) * g.qh[0]);
+        const T ldn0 = wdn0 * V1, lup0 = wup0 * V1;
+        const long long ro = (long long)i * L;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int x = xs[j];
+            if (j == E - 1 && x >= L) break;
+            const T F1 = F[q2s[j]], F2 = F[n2 + q2s[j]];
+            const T ldn1 = wdn1 * V2[j], lup1 = wup1 * V2[j];
+            const T2 c = ld2(R0 + x), cL = ld2(R0 + x - 2), cR = ld2(R0 + x + 2);
+            const T2 cU = ld2(R0 + x + K2), cD = ld2(R0 + x - K2);
+            const T2 e1U = ld2(d1 + x + K2), e1D = ld2(d1 + x - K2);
+            const T2 e2L = ld2(d2 + x - 2), e2C = ld2(d2 + x), e2R = ld2(d2 + x + 2);
+            const T2 up0 = ld2(u0 + x - K2), dn0 = ld2(w0 + x + K2);
+            const T2 up1L = ld2(u1 + x - 2), up1C = ld2(u1 + x);
+            const T2 dn1C = ld2(w1 + x), dn1R = ld2(w1 + x + 2);
+            T acc0 = -gm * c.x, acc1 = -gm * c.y;
+            acc0 += s1a[j] * (F1 * cU.x - cq1 * e1U.x + ldn0 * dn0.x) - s0a[j] * (F1 * cD.x + cq1 * e1D.x + lup0 * up0.x);
+            acc1 += s1a[j] * (F1 * cU.y - cq1 * e1U.y + ldn0 * dn0.y) - s0a[j] * (F1 * cD.y + cq1 * e1D.y + lup0 * up0.y);
+            acc0 += s1b0[j] * (F2 * c.y - cq2 * e2C.y + ldn1 * dn1C.y) - s0b0[j] * (F2 * cL.y + cq2 * e2L.y + lup1 * up1L.y);
+            acc1 += s1b1[j] * (F2 * cR.x - cq2 * e2R.x + ldn1 * dn1R.x) - s0b1[j] * (F2 * c.x + cq2 * e2C.x + lup1 * up1C.x);
+            T2 r;
+            if (y) {
+                const T2 yv = ld2(yr + x);
+                r.x = yv.x + a.c * acc0;
+                r.y = yv.y + a.c * acc1;
+            } else {
+                r.x = a.c * acc0;
+                r.y = a.c * acc1;
+            }
+            *reinterpret_cast<T2 *>(out + ro + x) = r;
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename T>
 struct HInsertArgs {
     const char *in;

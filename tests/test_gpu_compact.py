@@ -62,6 +62,7 @@ CASES = [
     (2, [11, 16], [5, 6], 4),
     (2, [9, 10], [7, 3], 2),
     (3, [7, 8, 9], [3, 4, 2], 2),
+    (2, [8, 32], [6, 6], 4),       # the row kernel reading the derivative arrays (3 pairs per thread)
 ]
 
 
@@ -100,7 +101,7 @@ def test_compact_rhs_matches_oracle(d, nq, K, depth, prec, qs):
 
 @pytest.mark.parametrize("qs", [1, 2])
 @pytest.mark.parametrize("prec", [64, 32])
-@pytest.mark.parametrize("d,nq,K,depth", [CASES[0], CASES[3], CASES[5]])
+@pytest.mark.parametrize("d,nq,K,depth", [CASES[0], CASES[3], CASES[5], CASES[6]])
 def test_compact_rk4_matches_oracle(d, nq, K, depth, prec, qs):
     h, pb = _handle(d, nq, K, depth, prec, max_batch=2, qs=qs)
     with h:
