@@ -172,6 +172,13 @@ cudaError_t configure_deriv(int n) {
 template <typename T>
 void launch_deriv(const HDerivArgs<T> &a, int batch, cudaStream_t s) {
     const dim3 grid((a.lines + kPcrCols - 1) / kPcrCols, batch), block(kPcrCols, kPcrRows);
+    if (a.n <= 32 && a.levels <= 5) {   // a line per warp, shuffles
+        if (a.skew)
+            hderiv_warp_kernel<T, true><<<grid, block, 0, s>>>(a);
+        else
+            hderiv_warp_kernel<T, false><<<grid, block, 0, s>>>(a);
+        return;
+    }
     if (a.skew)
         hderiv_pcr_kernel<T, true><<<grid, block, deriv_smem<T>(a.n, true), s>>>(a);
     else

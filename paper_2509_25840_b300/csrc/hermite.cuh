@@ -146,6 +146,83 @@ __global__ void __launch_bounds__(kPcrCols * kPcrRows) hderiv_pcr_kernel(const H
     }
 }
 
+// The same compact derivative for lines of at most 32 points, a line per warp: lane r holds row
+// r, (B f)_r and every PCR level take register shuffles (the level's row multipliers are the
+// lane's registers), no block barrier between levels.  A block loads a tile of 32 lines into
+// shared memory with coalesced loads (row-padded to 33 columns), its 8 warps solve 4 lines each,
+// and the tile is stored back coalesced.
+template <typename T>
+__device__ __forceinline__ T warp_bf(T v, int r, int n) {
+    const T ca = T(7) / T(9), cb = T(1) / T(36);
+    const T p1 = __shfl_down_sync(0xffffffffu, v, 1), m1 = __shfl_up_sync(0xffffffffu, v, 1);
+    const T p2 = __shfl_down_sync(0xffffffffu, v, 2), m2 = __shfl_up_sync(0xffffffffu, v, 2);
+    return ca * ((r + 1 < n ? p1 : T(0)) - (r >= 1 ? m1 : T(0))) +
+           cb * ((r + 2 < n ? p2 : T(0)) - (r >= 2 ? m2 : T(0)));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_pcr(T d, const T *k1, const T *k2, int levels) {
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        if (l >= levels) break;
+        const int o = 1 << l;
+        const T dm = __shfl_up_sync(0xffffffffu, d, o), dp = __shfl_down_sync(0xffffffffu, d, o);
+        d -= k1[l] * dm + k2[l] * dp;   // the multipliers are zero where r -+ 2^l leaves the line
+    }
+    return d;
+}
+
+template <typename T, bool SKEW>
+__global__ void __launch_bounds__(kPcrCols * kPcrRows) hderiv_warp_kernel(const HDerivArgs<T> a) {
+    __shared__ T tile[32][kPcrCols + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y, n = a.n;
+    const int line = blockIdx.x * kPcrCols + tx;
+    const bool ok = line < a.lines;
+    const int outer = ok ? line / a.st : 0;
+    const long long base = (long long)outer * n * a.st + (ok ? line - outer * a.st : 0);
+    const T *f = reinterpret_cast<const T *>(a.in + (long long)blockIdx.y * a.in_state) + base;
+    {
+        T v[32 / kPcrRows];   // every load of the tile in flight before the first store
+#pragma unroll
+        for (int j = 0; j < 32 / kPcrRows; ++j) {
+            const int i = ty + j * kPcrRows;
+            v[j] = (ok && i < n) ? __ldg(f + (long long)i * a.st) : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < 32 / kPcrRows; ++j) tile[ty + j * kPcrRows][tx] = v[j];
+    }
+    // lane tx is row tx of the warp's lines: its multipliers of every level and 1 / (b h)
+    T k1[5], k2[5];
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        k1[l] = (l < a.levels && tx < n) ? a.coef[(long long)2 * l * n + tx] : T(0);
+        k2[l] = (l < a.levels && tx < n) ? a.coef[(long long)(2 * l + 1) * n + tx] : T(0);
+    }
+    const T binv = tx < n ? a.coef[(long long)2 * a.levels * n + tx] : T(0);
+    __syncthreads();
+#pragma unroll
+    for (int cc = 0; cc < kPcrCols / kPcrRows; ++cc) {   // 4 independent lines per warp, interleaved
+        const int c = ty + cc * kPcrRows;
+        const T v = tx < n ? tile[tx][c] : T(0);
+        T r = warp_pcr(warp_bf(v, tx, n), k1, k2, a.levels) * binv;    // A^{-1} B f / h
+        if constexpr (SKEW) {
+            const T yv = warp_pcr(v, k1, k2, a.levels) * binv;             // A^{-1} f / h
+            r = T(0.5) * (r + warp_bf(yv, tx, n));
+        }
+        __syncwarp();
+        if (tx < n) tile[tx][c] = r;
+    }
+    __syncthreads();
+    if (ok) {
+        T *o = a.out + (long long)blockIdx.y * a.out_state + base;
+#pragma unroll
+        for (int j = 0; j < 32 / kPcrRows; ++j) {
+            const int i = ty + j * kPcrRows;
+            if (i < n) o[(long long)i * a.st] = tile[i][tx];
+        }
+    }
+}
+
 // 45 (f+1 - f-1) - 9 (f+2 - f-2) + (f+3 - f-3) along q axis `s` of the point x (q index i)
 template <typename T>
 __device__ __forceinline__ T hstencil(const T *__restrict__ f, int x, int i, int N, int st) {
