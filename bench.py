@@ -71,15 +71,17 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="two_mode_32",
                     choices=["two_mode_32", "one_mode_64", "three_mode_20", "sweep",
-                             "two_mode_hermite"],
+                             "two_mode_hermite", "three_mode_hermite"],
                     help="two_mode_32 is the benchmark; the others are secondary measurements")
     ap.add_argument("--instances", type=int, default=64, help="sweep: instances in the batch")
     ap.add_argument("--error-instances", type=int, default=8,
                     help="sweep: instances re-run in FP64 for the per-instance error report")
     ap.add_argument("--hermite-k", type=int, default=10,
-                    help="two_mode_hermite: Hermite functions per mode")
+                    help="two_mode_hermite, three_mode_hermite: Hermite functions per mode")
     ap.add_argument("--q-scheme", type=int, default=0, choices=[0, 1, 2],
                     help="two_mode_hermite: q-derivatives, 0 explicit stencil, 1 compact (PCR), 2 its skew part")
+    ap.add_argument("--save-r2", default=None,
+                    help="secondary workloads: write the last timed response (numpy .npy) here")
     ap.add_argument("--profile-case", action="store_true",
                     help="run `--steps` RK4 steps of `--batch` random states of the workload "
                          "through chfpe_rk4_device (a small, fixed case for ncu)")
@@ -646,6 +648,28 @@ def run_extra(args, local):
                                2: "skew-symmetric compact (Sec. III B, two PCR solves)"}[args.q_scheme],
                               nt, nt, hcells, base.cells))
         unit_name = "R2 spectra"
+    elif args.workload == "three_mode_hermite":
+        nt = args.nt if args.nt != 64 else 128
+        base = inputs.three_mode_20(nt=nt)
+        K = args.hermite_k
+
+        def hgrid_of(k):
+            return inputs.Grid(nq=base.grid.nq, np=(k,) * 3, qmin=base.grid.qmin, qmax=base.grid.qmax,
+                               pmin=(0.0,) * 3, pmax=(1.0,) * 3)
+        hgrid = hgrid_of(K)
+        prec, dtype = 32, "f32"
+        h = chfpe.Handle(base.model, hgrid, depth=base.depth, dt=base.dt, precision=prec,
+                         max_batch=nt, stream=stream.cuda_stream, p_basis=1)
+        eq = h.equilibrate(args.eq_steps, 1e-10, max(1, args.eq_steps))
+        hcells = h.members * h.points
+        units = hcells * base.r2_state_steps()
+        step = lambda: h.response2(base.A, base.B, base.C, nt, nt, base.stride)
+        desc = ("three_mode_hermite: the three_mode_20 model (3 water-like modes, omega 0.5/1.0/1.6) "
+                "and q grid (20^3) with the momenta in %d^3 Hermite functions (Sec. III A, Appendix A), "
+                "explicit 6th-order q-derivatives, depth 2 (10 members), dt=0.002; TRT R2 on %dx%d "
+                "at dtau=0.1, all t1 branches batched; %d cells per state against %d on the 20^6 grid"
+                % (K, nt, nt, hcells, base.cells))
+        unit_name = "R2 spectra"
     else:
         n = args.instances
         wls = [inputs.sweep_instance(s) for s in range(n)]
@@ -673,10 +697,12 @@ def run_extra(args, local):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step()
+        result = step()
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
+    if args.save_r2 and args.steps > 0:
+        np.save(args.save_r2, np.asarray(result))
     st = h.stats()
     T = ev0.elapsed_time(ev1) / 1e3
     achieved = st["stage_bytes"] / (st["stage_ms"] / 1e3) / 1e9 if st["stage_ms"] > 0 else None
@@ -717,6 +743,28 @@ def run_extra(args, local):
             "f32_vs_f64": float(np.abs(R[32] - R[64]).max() / np.abs(R[64]).max()),
             "hermite_f64_vs_grid_32^4_f64": float(np.abs(R[64] - Rg).max() / np.abs(Rg).max()),
             "metric": "max |R2 - R2_ref| / max |R2_ref|"}
+    if args.workload == "three_mode_hermite":
+        line["s_per_spectrum"] = T / args.steps
+        if args.err_nt > 0:
+            # FP32 against FP64 from the same equilibrium, and K against K + 2 Hermite functions
+            # (FP64, each from its own equilibrium): the truncation of the momentum basis
+            n = args.err_nt
+            Ceq = h.get_equilibrium()
+            R = {}
+            for prec_e in (32, 64):
+                with chfpe.Handle(base.model, hgrid, depth=base.depth, dt=base.dt, precision=prec_e,
+                                  max_batch=n, stream=stream.cuda_stream, p_basis=1) as he:
+                    he.set_equilibrium(Ceq)
+                    R[prec_e] = he.response2(base.A, base.B, base.C, n, n, base.stride)
+            with chfpe.Handle(base.model, hgrid_of(K + 2), depth=base.depth, dt=base.dt, precision=64,
+                              max_batch=n, stream=stream.cuda_stream, p_basis=1) as hk:
+                hk.equilibrate(args.eq_steps, 1e-10, max(1, args.eq_steps))
+                Rk = hk.response2(base.A, base.B, base.C, n, n, base.stride)
+            line["error"] = {
+                "samples": "%dx%d at dtau=0.1 (t1, t2 <= %.1f)" % (n, n, (n - 1) * 0.1),
+                "f32_vs_f64": float(np.abs(R[32] - R[64]).max() / np.abs(R[64]).max()),
+                "K_vs_K+2_f64": float(np.abs(R[64] - Rk).max() / np.abs(Rk).max()),
+                "metric": "max |R2 - R2_ref| / max |R2_ref|"}
     if args.workload == "sweep" and args.error_instances > 0:
         # error of the FP32 + bf16-tier propagation against FP64, per instance: the first
         # instances, from the same stored equilibria, R1 over 200 steps (21 samples)
