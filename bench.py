@@ -566,11 +566,11 @@ def run_profile_case(args):
     from paper_2509_25840_b300 import chfpe
     if args.variant is not None:
         os.environ["CHFPE_STAGE_VARIANT"] = str(args.variant)
-    if args.workload == "two_mode_hermite":
-        wl = inputs.two_mode_32()
-        K = args.hermite_k
-        grid = inputs.Grid(nq=wl.grid.nq, np=(K, K), qmin=wl.grid.qmin, qmax=wl.grid.qmax,
-                           pmin=(0.0, 0.0), pmax=(1.0, 1.0))
+    if args.workload in ("two_mode_hermite", "three_mode_hermite"):
+        wl = inputs.two_mode_32() if args.workload == "two_mode_hermite" else inputs.three_mode_20()
+        K, d = args.hermite_k, wl.grid.d
+        grid = inputs.Grid(nq=wl.grid.nq, np=(K,) * d, qmin=wl.grid.qmin, qmax=wl.grid.qmax,
+                           pmin=(0.0,) * d, pmax=(1.0,) * d)
         h = chfpe.Handle(wl.model, grid, depth=wl.depth, dt=wl.dt, precision=args.precision,
                          max_batch=args.batch, p_basis=1, q_scheme=args.q_scheme)
     else:

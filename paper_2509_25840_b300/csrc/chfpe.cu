@@ -246,7 +246,7 @@ static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *
     if (h->basis) {
         HStageArgs<T> a = hstage_args<T>(h);
         a.c = (T)c;
-        if (!h->qscheme) {
+        if (!h->dq) {
             a.in = (const char *)in;
             a.y = (const char *)y;
             a.out = (char *)out;
@@ -256,8 +256,9 @@ static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *
             ++h->launches;
             return CHFPE_OK;
         }
-        // compact q-derivatives: per chunk of states the derivative arrays hold, one PCR pass per q axis into the
-        // derivative arrays, then the stage kernel reading them
+        // derivative arrays: per chunk of states they hold, the compact q-derivatives (one PCR
+        // pass per q axis) or the explicit stencil sums of every q axis (one pass), then the stage
+        // kernel reading them
         const long long sbytes = a.state_bytes;
         a.dq = (const T *)h->dq;
         a.dq_state = h->state;
@@ -265,7 +266,13 @@ static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *
         for (int b0 = 0; b0 < batch; b0 += cap) {
             const int nb = std::min(cap, batch - b0);
             const long long off = (long long)b0 * sbytes;
-            for (int s = 0; s < h->d; ++s) {
+            if (!h->qscheme) {
+                launch_hstencil_sums<T>(h->d, a.g, (const char *)in + off, sbytes, (T *)h->dq, h->state,
+                                        h->M, nb, h->stream);
+                CK(cudaGetLastError());
+                ++h->launches;
+            }
+            for (int s = 0; s < h->d && h->qscheme; ++s) {
                 HDerivArgs<T> da;
                 da.in = (const char *)in + off;
                 da.in_state = sbytes;
@@ -851,11 +858,15 @@ static chfpe_status create_impl(const chfpe_model *model, const chfpe_grid *grid
         if (ce == cudaSuccess && h->prec == 32) ce = configure_hstage<float>();
         if (ce != cudaSuccess) st = fail(CHFPE_ECUDA, std::string("stage shared memory: ") + cudaGetErrorString(ce));
     }
-    if (!st && h->qscheme) {
-        // max(1, max_batch) states in the handle's precision, and at least one FP64 state (the
-        // FP64 equilibration of an FP32 handle runs through the same arrays)
+    if (!st && h->basis && (h->qscheme || d == 3)) {
+        // q-derivative arrays (the compact scheme's solutions; for three modes with the explicit
+        // stencil its sums, formed once per value): max(1, max_batch) states in the handle's
+        // precision, and at least one FP64 state (the FP64 equilibration of an FP32 handle runs
+        // through the same arrays)
         h->dq_bytes = (size_t)d * h->state * std::max<size_t>((size_t)std::max(1, opts->max_batch) * h->esize, 8);
         h->dq = (void *)dalloc<char>(h->dq_bytes, &st);
+    }
+    if (!st && h->qscheme) {
         // PCR tables (Sec. III C) of A = tridiag(1/3, 1, 1/3) per q axis, in FP64, then stored in
         // the handle precision: [levels][2][n] multipliers, [n] 1 / (b_i h)
         std::vector<double> tab;

@@ -209,6 +209,30 @@ bool launch_hstage<double>(int d, int depth, const HStageArgs<double> &a, int ba
     return launch_any<double>(d, depth, a, batch, s);
 }
 
+namespace {
+template <typename T>
+void stencil_sums(int d, const HGeo<T> &g, const char *in, long long in_state, T *out, long long state,
+                  int members, int batch, cudaStream_t s) {
+    const long long total = (long long)members * g.P;
+    const dim3 grid((unsigned)((total + 255) / 256), batch);
+    if (d == 3) hstencil_sums_kernel<T, 3><<<grid, 256, 0, s>>>(g, in, in_state, out, state, total);
+    else if (d == 2) hstencil_sums_kernel<T, 2><<<grid, 256, 0, s>>>(g, in, in_state, out, state, total);
+    else hstencil_sums_kernel<T, 1><<<grid, 256, 0, s>>>(g, in, in_state, out, state, total);
+}
+}  // namespace
+
+template <>
+void launch_hstencil_sums<float>(int d, const HGeo<float> &g, const char *in, long long in_state, float *out,
+                                 long long state, int members, int batch, cudaStream_t s) {
+    stencil_sums<float>(d, g, in, in_state, out, state, members, batch, s);
+}
+
+template <>
+void launch_hstencil_sums<double>(int d, const HGeo<double> &g, const char *in, long long in_state, double *out,
+                                  long long state, int members, int batch, cudaStream_t s) {
+    stencil_sums<double>(d, g, in, in_state, out, state, members, batch, s);
+}
+
 template <>
 cudaError_t configure_hstage<float>() { return configure_row<float>(); }
 

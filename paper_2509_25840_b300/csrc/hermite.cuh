@@ -235,6 +235,26 @@ __device__ __forceinline__ T hstencil(const T *__restrict__ f, int x, int i, int
     return T(45) * (p1 - m1) - T(9) * (p2 - m2) + (p3 - m3);
 }
 
+// Explicit q-stencil sums of every value along every q axis into the derivative arrays:
+//   out[b][s][x] = 45 (c_{+1} - c_{-1}) - 9 (c_{+2} - c_{-2}) + (c_{+3} - c_{-3})   along q_s,
+// zero values outside the q-grid (the stage kernel scales them by cq_s, which carries 1 / 60 h).
+// For three modes, where the stage's gather form would re-form the stencils of both ladder
+// neighbours of every value; one thread per value of every member.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) hstencil_sums_kernel(const HGeo<T> g, const char *in, long long in_state,
+                                                            T *out, long long out_state, long long total) {
+    const long long x = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (x >= total) return;
+    const T *c = reinterpret_cast<const T *>(in + (long long)blockIdx.y * in_state);
+    T *o = out + (long long)blockIdx.y * D * out_state;
+    const int r = (int)(x % g.P);                       // index inside the member
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+        const int i = (r / g.st[s]) % g.n[s];
+        o[(long long)s * out_state + x] = hstencil<T>(c + x, 0, i, g.n[s], g.st[s]);
+    }
+}
+
 // one RK4 stage, one thread per (q, k) point for every member (gather form: each output reads the
 // q-stencils of its k +- e_s neighbours and the link values of its member neighbours)
 template <typename T, int D, int DEPTH, int NT, bool PRE = false>
@@ -849,6 +869,18 @@ template <>
 cudaError_t configure_hstage<float>();
 template <>
 cudaError_t configure_hstage<double>();
+
+// explicit q-stencil sums of `batch` states (`state` values each) along every q axis into the
+// derivative arrays out[b][s][state] (hstencil_sums_kernel), for d = 3
+template <typename T>
+void launch_hstencil_sums(int d, const HGeo<T> &g, const char *in, long long in_state, T *out,
+                          long long state, int members, int batch, cudaStream_t s);
+template <>
+void launch_hstencil_sums<float>(int d, const HGeo<float> &g, const char *in, long long in_state, float *out,
+                                 long long state, int members, int batch, cudaStream_t s);
+template <>
+void launch_hstencil_sums<double>(int d, const HGeo<double> &g, const char *in, long long in_state, double *out,
+                                  long long state, int members, int batch, cudaStream_t s);
 
 // compact derivative along one q axis of `batch` states (hderiv_pcr_kernel); configure_hderiv
 // opts the kernels into the shared memory lines of n points need (once, before any launch or
