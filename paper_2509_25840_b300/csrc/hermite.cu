@@ -13,7 +13,18 @@ constexpr int kHNT = 128;
 // row-marching kernel (two modes, explicit stencils): shared memory per block (rows long enough
 // that fewer than two blocks fit on an SM run the gather kernel: measured faster there), grid size
 constexpr size_t kRowSmemMax = 112 * 1024;
-constexpr int kRowTargetBlocks = 148 * 8;
+// blocks wanted per launch: 8 per SM (about three waves at the kernels' 3 blocks per SM)
+int row_target_blocks() {
+    static int target = 0;
+    if (target == 0) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 148;
+        target = 8 * sms;
+    }
+    return target;
+}
 
 template <typename T>
 int row_pad(int KK) {
@@ -67,6 +78,7 @@ size_t rowpre_smem(long long L, int K2, int n2) {
 template <typename T>
 cudaError_t configure_row() {
     if (row_configured<T>()) return cudaSuccess;
+    (void)row_target_blocks();   // the device query before any stream capture
     cudaError_t e = configure_row_one<T, 1>();
     if (e == cudaSuccess) e = configure_row_one<T, 2>();
     if (e == cudaSuccess) e = configure_row_one<T, 3>();
@@ -98,7 +110,7 @@ bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
     const size_t smem = pre ? rowpre_smem<T>(L, K2, n2) : row_smem<T>(L, KK, K2, n2, pair);
     if (E > 8 || smem > kRowSmemMax || !row_configured<T>()) return false;
     const int per = M * batch;
-    const int chunks = std::max(1, std::min(pre ? n1 : n1 / 4, (kRowTargetBlocks + per - 1) / per));
+    const int chunks = std::max(1, std::min(pre ? n1 : n1 / 4, (row_target_blocks() + per - 1) / per));
     HRowArgs<T> ra;
     memset(&ra, 0, sizeof(ra));
     ra.s = a;

@@ -95,6 +95,28 @@ def test_hermite_rhs_matches_oracle(d, nq, K, depth, prec):
 
 
 @pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("d,nq,K,depth", [CASES[2], CASES[4], CASES[8]])
+def test_hermite_rhs_with_pointers_off_the_vector_boundaries(d, nq, K, depth, prec):
+    """Two states starting one element past a 16-byte boundary: the aligned paths (element pairs,
+    16-byte row copies) must step aside for the scalar row kernel with element copies, or the
+    gather kernel, and give the same result."""
+    model, grid, h, pb = _setup(d, nq, K, depth, prec, max_batch=2)
+    with h:
+        C = np.stack([_rounded(_random(pb, 21), prec), _rounded(_random(pb, 22), prec)])
+        want = [oracle.h_rhs(pb, C[b]) for b in range(2)]
+        n = C[0].size
+        x = torch.zeros(2 * n + 1, dtype=_dtype(prec), device="cuda")
+        y = torch.zeros(2 * n + 1, dtype=_dtype(prec), device="cuda")
+        x[1:] = torch.tensor(C.reshape(-1), dtype=_dtype(prec), device="cuda")
+        es = x.element_size()
+        h.rhs_device(x.data_ptr() + es, y.data_ptr() + es, 2)
+        got = y[1:].double().cpu().numpy().reshape(C.shape)
+    tol = 1e-13 if prec == 64 else 3e-6
+    for b in range(2):
+        assert np.abs(got[b] - want[b]).max() <= tol * np.abs(want[b]).max()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("d,nq,K,depth", [CASES[0], CASES[2], CASES[4], CASES[5], CASES[7], CASES[8]])
 def test_hermite_rk4_insert_observe_match_oracle(d, nq, K, depth, prec):
     model, grid, h, pb = _setup(d, nq, K, depth, prec, max_batch=2)
