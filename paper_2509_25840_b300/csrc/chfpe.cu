@@ -266,6 +266,18 @@ static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *
         for (int b0 = 0; b0 < batch; b0 += cap) {
             const int nb = std::min(cap, batch - b0);
             const long long off = (long long)b0 * sbytes;
+            a.in = (const char *)in + off;
+            a.y = y ? (const char *)y + off : nullptr;
+            a.out = (char *)out + off;
+            // two modes, q_2 lines of at most 32 points: the row kernel solves them itself where it
+            // runs (then there is no q_2 PCR pass)
+            a.c2 = nullptr;
+            if (h->qscheme && h->d == 2 && h->n[1] <= 32) {
+                a.c2 = (const T *)(sizeof(T) == 8 ? h->pcr : h->pcr32) + h->pcr_off[1];
+                a.lv2 = h->pcr_levels[1];
+                a.skew2 = h->qscheme == 2 ? 1 : 0;
+                if (!hstage_solves_q2<T>(h->d, h->depth, a)) a.c2 = nullptr;
+            }
             if (!h->qscheme) {
                 launch_hstencil_sums<T>(h->d, a.g, (const char *)in + off, sbytes, (T *)h->dq, h->state,
                                         h->M, nb, h->stream);
@@ -273,6 +285,7 @@ static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *
                 ++h->launches;
             }
             for (int s = 0; s < h->d && h->qscheme; ++s) {
+                if (s == 1 && a.c2) continue;
                 HDerivArgs<T> da;
                 da.in = (const char *)in + off;
                 da.in_state = sbytes;
@@ -288,9 +301,6 @@ static chfpe_status stage(chfpe_handle *h, const void *in, const void *y, void *
                 CK(cudaGetLastError());
                 ++h->launches;
             }
-            a.in = (const char *)in + off;
-            a.y = y ? (const char *)y + off : nullptr;
-            a.out = (char *)out + off;
             if (!launch_hstage<T>(h->d, h->depth, a, nb, h->stream))
                 return fail(CHFPE_EINVAL, "unsupported (d, depth)");
             CK(cudaGetLastError());

@@ -91,6 +91,27 @@ cudaError_t configure_row() {
     return e;
 }
 
+// the row kernel for two modes: element pairs or not, values (pairs) per thread, shared memory;
+// false where it does not apply (the gather kernel runs)
+template <typename T>
+bool row_plan(const HStageArgs<T> &a, bool &pair, int &E, size_t &smem) {
+    const int n2 = a.g.n[1], K2 = a.g.n[3], KK = a.g.n[2] * K2;
+    const long long L = (long long)n2 * KK;
+    // element pairs: even K_2, every pair 2-vector aligned
+    const uintptr_t al2 = 2 * sizeof(T) - 1;
+    pair = K2 % 2 == 0 && ((uintptr_t)a.in & al2) == 0 && ((uintptr_t)a.out & al2) == 0 &&
+           ((uintptr_t)a.y & al2) == 0 && (a.state_bytes & (long long)al2) == 0;
+    E = (int)((L + (pair ? 2 : 1) * kRowThreads - 1) / ((pair ? 2 : 1) * kRowThreads));
+    // compact derivatives: the pair kernel reading the derivative arrays (aligned like the state);
+    // solving the q_2 lines itself needs lines of at most 32 points
+    const bool pre = a.dq != nullptr;
+    if (pre && (!pair || ((uintptr_t)a.dq & al2) != 0 || (a.dq_state * (long long)sizeof(T)) % (2 * sizeof(T)) != 0))
+        return false;
+    if (a.c2 && (!pre || n2 > 32 || a.lv2 > 5)) return false;
+    smem = pre ? rowpre_smem<T>(L, K2, n2) : row_smem<T>(L, KK, K2, n2, pair);
+    return E <= 8 && smem <= kRowSmemMax && row_configured<T>();
+}
+
 template <typename T, int K>
 bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
     constexpr MemberTable<2, K> tab{};
@@ -98,17 +119,11 @@ bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
     static_assert(M <= kRowMaxM, "member table of the row kernel");
     const int n1 = a.g.n[0], n2 = a.g.n[1], K2 = a.g.n[3], KK = a.g.n[2] * K2;
     const long long L = (long long)n2 * KK;
-    // element pairs: even K_2, every pair 2-vector aligned
-    const uintptr_t al2 = 2 * sizeof(T) - 1;
-    const bool pair = K2 % 2 == 0 && ((uintptr_t)a.in & al2) == 0 && ((uintptr_t)a.out & al2) == 0 &&
-                      ((uintptr_t)a.y & al2) == 0 && (a.state_bytes & (long long)al2) == 0;
-    const int E = (int)((L + (pair ? 2 : 1) * kRowThreads - 1) / ((pair ? 2 : 1) * kRowThreads));
-    // compact derivatives: the pair kernel reading the derivative arrays (aligned like the state)
+    bool pair = false;
+    int E = 0;
+    size_t smem = 0;
+    if (!row_plan(a, pair, E, smem)) return false;
     const bool pre = a.dq != nullptr;
-    if (pre && (!pair || ((uintptr_t)a.dq & al2) != 0 || (a.dq_state * (long long)sizeof(T)) % (2 * sizeof(T)) != 0))
-        return false;
-    const size_t smem = pre ? rowpre_smem<T>(L, K2, n2) : row_smem<T>(L, KK, K2, n2, pair);
-    if (E > 8 || smem > kRowSmemMax || !row_configured<T>()) return false;
     const int per = M * batch;
     const int chunks = std::max(1, std::min(pre ? n1 : n1 / 4, (row_target_blocks() + per - 1) / per));
     HRowArgs<T> ra;
@@ -244,6 +259,20 @@ void launch_hstencil_sums<double>(int d, const HGeo<double> &g, const char *in, 
                                   long long state, int members, int batch, cudaStream_t s) {
     stencil_sums<double>(d, g, in, in_state, out, state, members, batch, s);
 }
+
+template <typename T>
+bool solves_q2(int d, int depth, const HStageArgs<T> &a) {
+    bool pair = false;
+    int E = 0;
+    size_t smem = 0;
+    return d == 2 && depth <= 5 && a.dq && a.c2 && row_plan(a, pair, E, smem);
+}
+
+template <>
+bool hstage_solves_q2<float>(int d, int depth, const HStageArgs<float> &a) { return solves_q2(d, depth, a); }
+
+template <>
+bool hstage_solves_q2<double>(int d, int depth, const HStageArgs<double> &a) { return solves_q2(d, depth, a); }
 
 template <>
 cudaError_t configure_hstage<float>() { return configure_row<float>(); }

@@ -53,6 +53,9 @@ struct HStageArgs {
     T c;
     const T *dq;                // compact scheme: d/dq_s of state b at dq + (b D + s) dq_state
     long long dq_state;         // (elements; nullptr: explicit stencils, cq holds 1/(60 h) then)
+    const T *c2;                // compact scheme, two modes, n_2 <= 32: the q_2 axis' PCR table
+    int lv2, skew2;             // ([lv2][2][n_2], then 1 / (b h)) for a row kernel that solves the
+                                // q_2 lines itself (hstage_solves_q2); skew2: the skew part
     HGeo<T> g;
 };
 
@@ -694,7 +697,8 @@ __global__ void __launch_bounds__(kRowThreads, 3) hstage_rowpre_kernel(const HRo
     const T *y = a.y ? reinterpret_cast<const T *>(a.y + boff) + (long long)m * g.P : nullptr;
     const T *dq = a.dq + (long long)blockIdx.z * 2 * a.dq_state + (long long)m * g.P;
     const bool vec = ra.vec != 0;
-    const T *src[8] = {in + (long long)m * g.P, dq, dq + a.dq_state, y,
+    const bool own2 = a.c2 != nullptr;   // D_2 c solved here from the centre row
+    const T *src[8] = {in + (long long)m * g.P, dq, own2 ? nullptr : dq + a.dq_state, y,
                        mt[2] >= 0 ? in + (long long)mt[2] * g.P : nullptr,
                        mt[3] >= 0 ? in + (long long)mt[3] * g.P : nullptr,
                        mt[4] >= 0 ? in + (long long)mt[4] * g.P : nullptr,
@@ -728,6 +732,17 @@ __global__ void __launch_bounds__(kRowThreads, 3) hstage_rowpre_kernel(const HRo
     };
     if (r0 < r1) issue(r0);
     asm volatile("cp.async.commit_group;" ::: "memory");
+    // q_2 lines: lane r is row r (q_2 = r) of a line; the PCR multipliers of every level, 1 / (b h)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T pk1[5], pk2[5], pbinv = T(0);
+    if (own2) {
+#pragma unroll
+        for (int l = 0; l < 5; ++l) {
+            pk1[l] = (l < a.lv2 && lane < n2) ? a.c2[(long long)2 * l * n2 + lane] : T(0);
+            pk2[l] = (l < a.lv2 && lane < n2) ? a.c2[(long long)(2 * l + 1) * n2 + lane] : T(0);
+        }
+        pbinv = lane < n2 ? a.c2[(long long)2 * a.lv2 * n2 + lane] : T(0);
+    }
     int xs[E], q2s[E];
     T s1a[E], s0a[E], s1b0[E], s0b0[E], s1b1[E], s0b1[E], V2[E];
 #pragma unroll
@@ -753,6 +768,19 @@ __global__ void __launch_bounds__(kRowThreads, 3) hstage_rowpre_kernel(const HRo
         if (i + 1 < r1) issue(i + 1);   // into the buffer the previous row used
         asm volatile("cp.async.commit_group;" ::: "memory");
         const int b = i & 1;
+        if (own2) {
+            // D_2 c of the row: the compact derivative along q_2 of each of the K_1 K_2 lines
+            // (values KK apart), a line per warp, by register shuffles (as hderiv_warp_kernel)
+            const T *cr = buf + (b * 8) * SL;
+            T *d2w = buf + (b * 8 + 2) * SL;
+            for (int kk = warp; kk < KK; kk += kRowThreads / 32) {
+                const T v = lane < n2 ? cr[lane * KK + kk] : T(0);
+                T r = warp_pcr(warp_bf(v, lane, n2), pk1, pk2, a.lv2) * pbinv;
+                if (a.skew2) r = T(0.5) * (r + warp_bf(warp_pcr(v, pk1, pk2, a.lv2) * pbinv, lane, n2));
+                if (lane < n2) d2w[lane * KK + kk] = r;
+            }
+            __syncthreads();
+        }
         const T *R0 = buf + (b * 8) * SL, *d1 = R0 + SL, *d2 = R0 + 2 * SL, *yr = R0 + 3 * SL;
         const T *u0 = R0 + 4 * SL, *u1 = R0 + 5 * SL, *w0 = R0 + 6 * SL, *w1 = R0 + 7 * SL;
         const T *F = fr + b * 2 * n2;
@@ -860,6 +888,15 @@ template <>
 bool launch_hstage<float>(int d, int depth, const HStageArgs<float> &a, int batch, cudaStream_t s);
 template <>
 bool launch_hstage<double>(int d, int depth, const HStageArgs<double> &a, int batch, cudaStream_t s);
+
+// whether the stage of `batch` states with these arguments (a.c2 set) runs the row kernel that
+// solves the compact q_2 lines itself, so that the caller leaves out the q_2 PCR pass
+template <typename T>
+bool hstage_solves_q2(int d, int depth, const HStageArgs<T> &a);
+template <>
+bool hstage_solves_q2<float>(int d, int depth, const HStageArgs<float> &a);
+template <>
+bool hstage_solves_q2<double>(int d, int depth, const HStageArgs<double> &a);
 
 // opts the row-marching stage kernels (hstage_row_kernel) into the shared memory they may use;
 // once per element type, before any launch or stream capture that uses them
