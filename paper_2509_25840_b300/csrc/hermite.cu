@@ -237,14 +237,27 @@ bool launch_hstage<double>(int d, int depth, const HStageArgs<double> &a, int ba
 }
 
 namespace {
+template <typename T, int V>
+void stencil_sums_v(int d, const HGeo<T> &g, const char *in, long long in_state, T *out, long long state,
+                    long long total, int batch, cudaStream_t s) {
+    const dim3 grid((unsigned)((total / V + 255) / 256), batch);
+    if (d == 3) hstencil_sums_kernel<T, 3, V><<<grid, 256, 0, s>>>(g, in, in_state, out, state, total);
+    else if (d == 2) hstencil_sums_kernel<T, 2, V><<<grid, 256, 0, s>>>(g, in, in_state, out, state, total);
+    else hstencil_sums_kernel<T, 1, V><<<grid, 256, 0, s>>>(g, in, in_state, out, state, total);
+}
+
 template <typename T>
 void stencil_sums(int d, const HGeo<T> &g, const char *in, long long in_state, T *out, long long state,
                   int members, int batch, cudaStream_t s) {
     const long long total = (long long)members * g.P;
-    const dim3 grid((unsigned)((total + 255) / 256), batch);
-    if (d == 3) hstencil_sums_kernel<T, 3><<<grid, 256, 0, s>>>(g, in, in_state, out, state, total);
-    else if (d == 2) hstencil_sums_kernel<T, 2><<<grid, 256, 0, s>>>(g, in, in_state, out, state, total);
-    else hstencil_sums_kernel<T, 1><<<grid, 256, 0, s>>>(g, in, in_state, out, state, total);
+    constexpr int V = 16 / sizeof(T);
+    // vectors: a q point's values (P / NQ of them) a multiple of V, 16-byte aligned states and arrays
+    const bool vec = (g.P / g.NQ) % V == 0 && ((uintptr_t)in & 15) == 0 && (in_state & 15) == 0 &&
+                     ((uintptr_t)out & 15) == 0 && (state * (long long)sizeof(T)) % 16 == 0;
+    if (vec)
+        stencil_sums_v<T, V>(d, g, in, in_state, out, state, total, batch, s);
+    else
+        stencil_sums_v<T, 1>(d, g, in, in_state, out, state, total, batch, s);
 }
 }  // namespace
 

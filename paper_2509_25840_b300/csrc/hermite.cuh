@@ -242,19 +242,36 @@ __device__ __forceinline__ T hstencil(const T *__restrict__ f, int x, int i, int
 //   out[b][s][x] = 45 (c_{+1} - c_{-1}) - 9 (c_{+2} - c_{-2}) + (c_{+3} - c_{-3})   along q_s,
 // zero values outside the q-grid (the stage kernel scales them by cq_s, which carries 1 / 60 h).
 // For three modes, where the stage's gather form would re-form the stencils of both ladder
-// neighbours of every value; one thread per value of every member.
-template <typename T, int D>
+// neighbours of every value; one thread per V consecutive values of every member (V > 1 where a
+// q point's K_1..K_D values are a multiple of V: the V values share their q indices, every tap is
+// one vector load).
+template <typename T, int D, int V>
 __global__ void __launch_bounds__(256) hstencil_sums_kernel(const HGeo<T> g, const char *in, long long in_state,
                                                             T *out, long long out_state, long long total) {
-    const long long x = (long long)blockIdx.x * 256 + threadIdx.x;
+    typedef typename VecOf<T, V>::type VT;
+    const long long x = ((long long)blockIdx.x * 256 + threadIdx.x) * V;
     if (x >= total) return;
-    const T *c = reinterpret_cast<const T *>(in + (long long)blockIdx.y * in_state);
-    T *o = out + (long long)blockIdx.y * D * out_state;
+    const T *c = reinterpret_cast<const T *>(in + (long long)blockIdx.y * in_state) + x;
+    T *o = out + (long long)blockIdx.y * D * out_state + x;
     const int r = (int)(x % g.P);                       // index inside the member
 #pragma unroll
     for (int s = 0; s < D; ++s) {
-        const int i = (r / g.st[s]) % g.n[s];
-        o[(long long)s * out_state + x] = hstencil<T>(c + x, 0, i, g.n[s], g.st[s]);
+        const int i = (r / g.st[s]) % g.n[s], st = g.st[s], n = g.n[s];
+        T acc[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) acc[e] = T(0);
+#pragma unroll
+        for (int t = 1; t <= 3; ++t) {
+            const T w = t == 1 ? T(45) : (t == 2 ? T(-9) : T(1));
+            VT p, m;
+            if (i + t < n) p = __ldg(reinterpret_cast<const VT *>(c + (long long)t * st));
+            if (i - t >= 0) m = __ldg(reinterpret_cast<const VT *>(c - (long long)t * st));
+            const T *pe = reinterpret_cast<const T *>(&p), *me = reinterpret_cast<const T *>(&m);
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                acc[e] += w * ((i + t < n ? pe[e] : T(0)) - (i - t >= 0 ? me[e] : T(0)));
+        }
+        *reinterpret_cast<VT *>(o + (long long)s * out_state) = *reinterpret_cast<const VT *>(acc);
     }
 }
 
