@@ -167,6 +167,17 @@ void launch_one(const HStageArgs<T> &a, int batch, cudaStream_t s) {
         if (launch_row<T, K>(a, batch, s)) return;
     }
     const dim3 grid((a.g.P + kHNT - 1) / kHNT, batch);
+    // derivative arrays in element pairs: even K_D, 2-vector aligned states and arrays
+    if constexpr (D >= 2) {
+        const uintptr_t al2 = 2 * sizeof(T) - 1;
+        if (a.dq && a.g.n[2 * D - 1] % 2 == 0 && ((uintptr_t)a.in & al2) == 0 &&
+            ((uintptr_t)a.out & al2) == 0 && ((uintptr_t)a.y & al2) == 0 && ((uintptr_t)a.dq & al2) == 0 &&
+            (a.state_bytes & (long long)al2) == 0 && a.dq_state % 2 == 0) {
+            const dim3 grid2((a.g.P / 2 + kHNT - 1) / kHNT, batch);
+            hstage_pre2_kernel<T, D, K, kHNT><<<grid2, kHNT, 0, s>>>(a);
+            return;
+        }
+    }
     if (a.dq)
         hstage_kernel<T, D, K, kHNT, true><<<grid, kHNT, 0, s>>>(a);
     else

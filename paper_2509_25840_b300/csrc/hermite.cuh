@@ -837,6 +837,131 @@ __global__ void __launch_bounds__(kRowThreads, 3) hstage_rowpre_kernel(const HRo
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// The gather stage reading the derivative arrays (compact scheme, or the three-mode stencil
+// sums) in element pairs: thread t owns the values x, x + 1 (x = 2t) of every member, the same q
+// point and k except k_D = kb, kb + 1 (kb even, K_D even); the neighbours along k_1..k_{D-1} are
+// 2-vector loads at x -+ stride, those along k_D come from the pairs at x - 2 and x + 2 (read
+// only where they lie inside the k_D row).  Equal to hstage_kernel<..., true> up to the order of
+// the additions.
+template <typename T, int D, int DEPTH, int NT>
+__global__ void __launch_bounds__(NT) hstage_pre2_kernel(const HStageArgs<T> a) {
+    typedef typename VecOf<T, 2>::type T2;
+    constexpr MemberTable<D, DEPTH> tab{};
+    constexpr int M = MemberTable<D, DEPTH>::M;
+    const HGeo<T> &g = a.g;
+    const int x = 2 * (blockIdx.x * NT + threadIdx.x);
+    if (x >= g.P) return;
+    const long long boff = (long long)blockIdx.y * a.state_bytes;
+    const T *in = reinterpret_cast<const T *>(a.in + boff);
+    T *out = reinterpret_cast<T *>(a.out + boff);
+    const T *y = a.y ? reinterpret_cast<const T *>(a.y + boff) : nullptr;
+    const T *dqb = a.dq + (long long)blockIdx.y * D * a.dq_state;
+    int idx[2 * D];
+    {
+        int r = x;
+#pragma unroll
+        for (int ax = 2 * D - 1; ax >= 0; --ax) {
+            idx[ax] = r % g.n[ax];
+            r /= g.n[ax];
+        }
+    }
+    const int qlin = x / g.Pk, KD = g.n[2 * D - 1], kb = idx[2 * D - 1];
+    const bool hl = kb >= 1, hr = kb + 2 < KD;      // the k_D neighbours x - 1 and x + 2 exist
+    T F[D], Vl[D], sk[D], sk1[D];
+    bool hp[D], hm[D];
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+        F[s] = __ldg(g.Fh + s * g.NQ + qlin);
+        const T q = g.qlo[s] + T(idx[s]) * g.qh[s];
+        Vl[s] = (g.VLL[s] + g.VSL[s] * q) * g.lk[s];
+        const int k = idx[D + s];
+        sk[s] = sqrt(T(k));
+        sk1[s] = sqrt(T(k + 1));
+        hp[s] = k + 1 < g.n[D + s];
+        hm[s] = k >= 1;
+    }
+    const T s0 = sqrt(T(kb)), s1 = sqrt(T(kb + 1)), s2 = sqrt(T(kb + 2));   // along k_D
+    auto ld = [](const T *p) { return __ldg(reinterpret_cast<const T2 *>(p)); };
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const T *c = in + (long long)m * g.P;
+        T gm = T(0);
+#pragma unroll
+        for (int s = 0; s < D; ++s) gm += T(tab.n[m][s]) * g.gam[s];
+        const T2 c0 = ld(c + x);
+        T acc0 = -gm * c0.x, acc1 = -gm * c0.y;
+#pragma unroll
+        for (int s = 0; s < D - 1; ++s) {            // k_s, s < D - 1: both values alike
+            const int e = g.st[D + s];
+            const T *dq = dqb + (long long)s * a.dq_state + (long long)m * g.P;
+            if (hp[s]) {
+                const T2 cp = ld(c + x + e), dp = ld(dq + x + e);
+                acc0 += sk1[s] * (F[s] * cp.x - g.cq[s] * dp.x);
+                acc1 += sk1[s] * (F[s] * cp.y - g.cq[s] * dp.y);
+                if (tab.dn[m][s] >= 0) {
+                    const T2 v = ld(in + (long long)tab.dn[m][s] * g.P + x + e);
+                    const T w = g.link[s][tab.n[m][s]] * Vl[s] * sk1[s];
+                    acc0 += w * v.x;
+                    acc1 += w * v.y;
+                }
+            }
+            if (hm[s]) {
+                const T2 cm = ld(c + x - e), dm = ld(dq + x - e);
+                acc0 -= sk[s] * (F[s] * cm.x + g.cq[s] * dm.x);
+                acc1 -= sk[s] * (F[s] * cm.y + g.cq[s] * dm.y);
+                if (tab.up[m][s] >= 0) {
+                    const T2 u = ld(in + (long long)tab.up[m][s] * g.P + x - e);
+                    const T w = g.link[s][tab.n[m][s] + 1] * Vl[s] * sk[s];
+                    acc0 -= w * u.x;
+                    acc1 -= w * u.y;
+                }
+            }
+        }
+        {                                            // k_D: values kb (x) and kb + 1 (x + 1)
+            constexpr int s = D - 1;
+            const T *dq = dqb + (long long)s * a.dq_state + (long long)m * g.P;
+            const T2 d0 = ld(dq + x);
+            // + sqrt(k+1) (F c - cq D)(k+1): x + 1 for the first value, x + 2 for the second
+            acc0 += s1 * (F[s] * c0.y - g.cq[s] * d0.y);
+            // - sqrt(k) (F c + cq D)(k-1): x - 1 for the first, x for the second
+            acc1 -= s1 * (F[s] * c0.x + g.cq[s] * d0.x);
+            if (hr) {
+                const T2 cr = ld(c + x + 2), dr = ld(dq + x + 2);
+                acc1 += s2 * (F[s] * cr.x - g.cq[s] * dr.x);
+            }
+            if (hl) {
+                const T2 cl = ld(c + x - 2), dl = ld(dq + x - 2);
+                acc0 -= s0 * (F[s] * cl.y + g.cq[s] * dl.y);
+            }
+            if (tab.dn[m][s] >= 0) {                 // + sqrt((n+1)... ) V' sqrt(k+1) c^(n-e)_{k+1}
+                const T *cd = in + (long long)tab.dn[m][s] * g.P;
+                const T w = g.link[s][tab.n[m][s]] * Vl[s];
+                const T2 v0 = ld(cd + x);
+                acc0 += w * s1 * v0.y;
+                if (hr) acc1 += w * s2 * ld(cd + x + 2).x;
+            }
+            if (tab.up[m][s] >= 0) {                 // - ... V' sqrt(k) c^(n+e)_{k-1}
+                const T *cu = in + (long long)tab.up[m][s] * g.P;
+                const T w = g.link[s][tab.n[m][s] + 1] * Vl[s];
+                const T2 u0 = ld(cu + x);
+                acc1 -= w * s1 * u0.x;
+                if (hl) acc0 -= w * s0 * ld(cu + x - 2).y;
+            }
+        }
+        const long long o = (long long)m * g.P + x;
+        T2 r;
+        if (y) {
+            const T2 yv = *reinterpret_cast<const T2 *>(y + o);   // y may be out itself
+            r.x = yv.x + a.c * acc0;
+            r.y = yv.y + a.c * acc1;
+        } else {
+            r.x = a.c * acc0;
+            r.y = a.c * acc1;
+        }
+        *reinterpret_cast<T2 *>(out + o) = r;
+    }
+}
+
 template <typename T>
 struct HInsertArgs {
     const char *in;
