@@ -163,7 +163,7 @@ chfpe_status chfpe_response3(chfpe_handle *h, const chfpe_optical *A, const chfp
 chfpe_status chfpe_save_equilibrium(const chfpe_handle *h, const char *path);
 chfpe_status chfpe_load_equilibrium(chfpe_handle *h, const char *path);
 
-/* ---- batches: many instances (models and grids) advanced together (BASELINE sweep config) -- */
+/* ---- batches: many instances (models and grids) advanced together (the parameter sweep) ------ */
 
 /* Create a batch of n instances (models[i], grids[i]) sharing one set of options (same number of
  * modes, depth, precision, bf16_tier; max_batch = the branch slots per instance that
