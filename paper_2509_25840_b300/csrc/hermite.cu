@@ -3,6 +3,7 @@
 #include "hermite.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 namespace chfpe {
@@ -13,6 +14,17 @@ constexpr int kHNT = 128;
 // row-marching kernel (two modes, explicit stencils): shared memory per block (rows long enough
 // that fewer than two blocks fit on an SM run the gather kernel: measured faster there), grid size
 constexpr size_t kRowSmemMax = 112 * 1024;
+// q_1 chunks per (state, member) fixed by CHFPE_HROW_CHUNKS (a tuning knob like
+// CHFPE_STAGE_VARIANT; 0 or unset: from the grid size below)
+int row_chunks_forced() {
+    static int c = -1;
+    if (c < 0) {
+        const char *e = std::getenv("CHFPE_HROW_CHUNKS");
+        c = e ? std::max(0, std::atoi(e)) : 0;
+    }
+    return c;
+}
+
 // blocks wanted per launch: 8 per SM (about three waves at the kernels' 3 blocks per SM)
 int row_target_blocks() {
     static int target = 0;
@@ -125,7 +137,8 @@ bool launch_row(const HStageArgs<T> &a, int batch, cudaStream_t s) {
     if (!row_plan(a, pair, E, smem)) return false;
     const bool pre = a.dq != nullptr;
     const int per = M * batch;
-    const int chunks = std::max(1, std::min(pre ? n1 : n1 / 4, (row_target_blocks() + per - 1) / per));
+    int chunks = std::max(1, std::min(pre ? n1 : n1 / 4, (row_target_blocks() + per - 1) / per));
+    if (row_chunks_forced() > 0) chunks = std::min(row_chunks_forced(), n1);
     HRowArgs<T> ra;
     memset(&ra, 0, sizeof(ra));
     ra.s = a;
