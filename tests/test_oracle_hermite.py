@@ -44,6 +44,42 @@ def test_ladder_generator_is_antisymmetric_minus_damping(d, n, K, depth):
     assert np.abs(M).max() > 1.0          # the operator is not trivially zero
 
 
+def test_three_mode_generator_is_antisymmetric_minus_damping_bilinear():
+    """Three modes (the water-like model: pair couplings, square-linear bath coupling), without
+    forming the matrix: for seeded u, v the bilinear form u.(M v) + v.(M u) equals
+    -2 sum_i u_i D_i v_i, D = sum_s n_s gamma_s per member, i.e. M + M^T = -2 D (a wrong sign,
+    index or factor on one of the q_3 / k_3 terms or links breaks the symmetry)."""
+    model = inputs.three_mode_model()
+    pb = oracle.Problem(model, _hgrid([7, 8, 7], [3, 2, 4], [4.0, 4.0, 4.0]), 2)
+    damp = np.repeat([sum(nn[s] * model.gamma[s] for s in range(3)) for nn in oracle.members(3, 2)], pb.P)
+    rng = np.random.default_rng(11)
+    N = pb.M * pb.P
+    for _ in range(3):
+        u, v = rng.normal(size=N), rng.normal(size=N)
+        Mu = oracle.h_rhs(pb, u.reshape(pb.state_shape)).ravel()
+        Mv = oracle.h_rhs(pb, v.reshape(pb.state_shape)).ravel()
+        lhs = u @ Mv + v @ Mu
+        rhs = -2.0 * np.sum(u * damp * v)
+        scale = np.abs(u) @ np.abs(Mv) + np.abs(v) @ np.abs(Mu)
+        assert abs(lhs - rhs) <= 1e-13 * scale, (lhs, rhs, scale)
+        assert np.abs(Mu).max() > 1.0        # the operator is not trivially zero
+
+
+def test_three_mode_boltzmann_is_stationary_at_sixth_order():
+    """The water-like model on q-domains where exp(-U/2kT) < 1e-7 at the ends: the residual of the
+    equilibrium coefficients falls at about sixth order in h_q."""
+    model = inputs.three_mode_model()
+    res = []
+    ns = (24, 32)
+    for n in ns:
+        g = inputs.default_grid(model, [n], cut=32.0)
+        pb = oracle.Problem(model, _hgrid([n] * 3, [2, 2, 2], list(g.qmax)), 1)
+        c = oracle.h_boltzmann(pb)
+        res.append(np.abs(oracle.h_rhs(pb, c)).max() / np.abs(c).max())
+    order = math.log(res[0] / res[1]) / math.log(ns[1] / ns[0])
+    assert res[1] < 1e-3 and order > 4.5, (res, order)
+
+
 @pytest.mark.parametrize("d,ns,K,L", [(1, (40, 80), [8], 7.5), (2, (24, 32), [4, 5], 5.5)])
 def test_boltzmann_is_stationary_at_sixth_order(d, ns, K, L):
     """(The q-domain reaches exp(-U/2kT) < 1e-7 at its ends, below the stencil error.)"""
