@@ -165,6 +165,28 @@ def test_printed_end_rows_give_a_growing_mode_and_the_skew_part_does_not():
     assert np.linalg.eigvals(M2).real.max() < 1e-9
 
 
+def test_three_mode_skew_generator_is_antisymmetric_minus_damping_bilinear():
+    """Three modes (the water-like model) with the skew-symmetric compact part on every q axis:
+    u.(M v) + v.(M u) = -2 sum u D v for seeded u, v (M + M^T = -2 diag(sum_s n_s gamma_s)
+    without forming M); with the printed end rows the same form is off by far more."""
+    model = inputs.three_mode_model()
+    grid = _hgrid([9, 8, 10], [3, 2, 2], [4.0, 4.0, 4.0])
+    pb = oracle.Problem(model, grid, 2, qscheme=2)
+    pb1 = oracle.Problem(model, grid, 2, qscheme=1)
+    damp = np.repeat([sum(nn[s] * model.gamma[s] for s in range(3)) for nn in oracle.members(3, 2)], pb.P)
+    rng = np.random.default_rng(5)
+    N = pb.M * pb.P
+    for _ in range(2):
+        u, v = rng.normal(size=N), rng.normal(size=N)
+        errs = []
+        for p_ in (pb, pb1):
+            Mu = oracle.h_rhs(p_, u.reshape(p_.state_shape)).ravel()
+            Mv = oracle.h_rhs(p_, v.reshape(p_.state_shape)).ravel()
+            scale = np.abs(u) @ np.abs(Mv) + np.abs(v) @ np.abs(Mu)
+            errs.append(abs(u @ Mv + v @ Mu + 2.0 * np.sum(u * damp * v)) / scale)
+        assert errs[0] < 1e-13 and errs[1] > 1e-6, errs
+
+
 def test_skew_part_is_antisymmetric_and_equals_the_compact_derivative_inside():
     n, h = 64, 0.1
     D = np.stack([oracle.compact_skew_deriv1d(np.eye(n)[j], h) for j in range(n)], axis=1)
